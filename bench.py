@@ -1,0 +1,329 @@
+"""Benchmark: particle-steps/s of the perfect-dispersion PIC step on one GB300.
+
+Default workload (c1): 1536x256x256 cells, dx = lambda0/24, dy = dz = lambda0/3,
+lambda0 = 0.8 um, 2 electrons per cell on a jittered lattice, n = 0.004 n_c
+behind a 50 um up-ramp, a0 = 4, 30 fs, 16 um waist, moving window at c, FP64.
+The timed steps are steps S..S+K of the 1000-step run, S = --start-step
+(default 900): the window and laser are placed where they are at step S with
+the plasma that has entered by then loaded cold, so every timed step pushes
+the particle count of the late run.  A step is the whole path: gather, Boris
+push, Esirkepov deposit, field update, window shift, absorption, injection.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica (the path is not
+sharded across GPUs here): weak scaling, no data-path collective; the timed
+region is bracketed by barriers and the max over ranks is reported.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (cubic gather+Boris+deposit+field), FP32/batched vs FP64, 1 GB300"
+UNIT = "particle-steps/s"
+# algorithmic cost per particle push of the gather/push/deposit kernel
+FLOP_PER_PARTICLE = 2496  # counted operation by operation in the design doc
+BYTES_PER_PARTICLE = {"fp64": 120, "fp32": 60}  # read + write of the SoA record
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c4"])
+    ap.add_argument("--start-step", type=int, default=-1)
+    ap.add_argument("--crop", default="", help="nx,ny,nz (profiling small cases)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(args):
+    from paper_1204_0838_gb300 import workloads as W
+    start = args.start_step
+    if start < 0:
+        start = {"c0": 0, "c1": 900, "c2": 900, "c4": 4500}[args.config]
+    crop = tuple(int(v) for v in args.crop.split(",")) if args.crop else None
+    cfg = W.config(args.config, crop=crop, start_step=start)
+    return cfg, start
+
+
+def _describe(cfg, start, precision):
+    return {"workload": "%s: %dx%dx%d cells, dx=lambda0/%g, dy=dz=lambda0/%g, %d ppc %s, %s, "
+            "a0=%g, %s, steps %d.. of the %d-step run" % (
+                cfg["name"], cfg["nx"], cfg["ny"], cfg["nz"], cfg["lambda0"] / cfg["dx"],
+                cfg["lambda0"] / cfg["dy"], cfg["ppc"], cfg["loading"],
+                "moving window at c" if cfg["window"] else "no window", cfg["a0"], precision,
+                start, cfg["steps"]),
+            "grid": [cfg["nx"], cfg["ny"], cfg["nz"]], "ppc": cfg["ppc"], "start_step": start,
+            "precision": precision,
+            "l2": "inputs larger than L2 (fields and particles are GBs), no flush"}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "pic_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _fp_peak_tflops(precision, sm_mhz):
+    """ALU peak from unit counts and clock: 152 SMs x FMA lanes per SM x 2 flop.
+    FP32: 128 lanes/SM.  FP64: 1.25 TFLOP/s nominal for the part at 2.07 GHz,
+    i.e. 2 FMA lanes per SM."""
+    lanes = 128 if precision == "fp32" else 2
+    return 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
+
+
+def _oracle_sample():
+    """The FP64 CPU oracle on a bounded sample of the c1 workload: the c1
+    spacings, loading and laser on a 64x48x48 window that the plasma fills
+    (about 2.9e5 particles), single-threaded."""
+    from oracle import oracle as O
+    from paper_1204_0838_gb300 import workloads as W
+    cfg = W.config("c1", crop=(64, 48, 48), start_step=2000)
+    o = O.Sim(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"], cfg["lambda0"],
+              x0=cfg["x0"], periodic_x=False, seed=cfg["seed"], window=cfg["window"])
+    o.add_species(cfg["prof_x"], cfg["prof_n"], cfg["ppc"], loading=cfg["loading"])
+    o.add_laser(cfg["a0"], cfg["waist"], cfg["fwhm"], cfg["lambda0"], cfg["x_focus"], cfg["t_peak"])
+    desc = ("FP64 C oracle, 1 thread, c1 spacings/loading/laser on a 64x48x48 window filled with "
+            "plasma (%d particles)" % o.info()["np"])
+    return o, desc
+
+
+def _time_oracle(o, steps):
+    pushed = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        pushed += o.info()["np"]
+        o.step(1)
+    return pushed, time.perf_counter() - t0
+
+
+def _oracle_sample_rate(seconds_target=12.0):
+    o, desc = _oracle_sample()
+    o.step(1)
+    pushed, dt = _time_oracle(o, 2)
+    steps = 2
+    while dt < seconds_target:
+        p, d = _time_oracle(o, 2)
+        pushed += p
+        dt += d
+        steps += 2
+    return pushed / dt, desc + ", %d steps" % steps, steps
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, on the host cores (rank 0 only)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import build as ob
+    ob.build()
+    cfg, start = _workload(args)
+    o, desc = _oracle_sample()
+    _time_oracle(o, args.warmup)
+    pushed, dt = _time_oracle(o, args.steps)
+    value = pushed / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference", "config": _describe(cfg, start, "fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc + "; each timed step is one step of this sample"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_1204_0838_gb300 import build as pb
+    from paper_1204_0838_gb300 import pic
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    pb.build()
+    cfg, start = _workload(args)
+    precision = cfg["precision"]
+    g = pic.Sim(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"], cfg["lambda0"],
+                x0=cfg["x0"], periodic_x=cfg["periodic_x"], precision=precision, seed=cfg["seed"] + rank,
+                window=cfg["window"])
+    g.add_species(cfg["prof_x"], cfg["prof_n"], cfg["ppc"], loading=cfg["loading"])
+    g.add_laser(cfg["a0"], cfg["waist"], cfg["fwhm"], cfg["lambda0"], cfg["x_focus"], cfg["t_peak"])
+    for _ in range(args.warmup):
+        g.step(1)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    pushed0 = g.info()["pushed"]
+    pic.pic_timing_start(g.h, True)
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    pic.pic_step(g.h, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    timing = pic.pic_timing_read(g.h)
+    pic.pic_timing_start(g.h, False)
+    info = g.info()
+    pushed = info["pushed"] - pushed0
+    # max time / summed particle-steps over ranks
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+        c = torch.tensor([float(pushed)], dtype=torch.float64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        pushed = float(c[0])
+    value = pushed / (ms / 1e3)
+
+    # end to end through the C-ABI: one pic_step per step plus the field
+    # energy read back into a host buffer, wall clock
+    t0 = time.perf_counter()
+    pushed_e0 = g.info()["pushed"]
+    for _ in range(args.steps):
+        pic.pic_step(g.h, 1)
+        g.diag("field_energy")
+    t1 = time.perf_counter()
+    pushed_e = g.info()["pushed"] - pushed_e0
+    e2e = pushed_e / (t1 - t0)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t1 - t0], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([float(pushed_e)], dtype=torch.float64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        e2e = float(c[0]) / float(t[0])
+
+    peaks, src = _peaks()
+    k2_ms = timing["ms"]["gather_push_deposit"]
+    k2_n = max(timing["launches"]["gather_push_deposit"], 1)
+    per_launch_pushes = (info["pushed"] - pushed0) / k2_n
+    avg_s = k2_ms / 1e3 / k2_n
+    sm_clock = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    achieved = FLOP_PER_PARTICLE * per_launch_pushes / avg_s / 1e12 if avg_s > 0 else 0.0
+    peak = _fp_peak_tflops(precision, peaks.get("sm_max_mhz", 2070.0))
+    roofline = {"kernel": "k_push_deposit (gather + Boris + Esirkepov deposit)",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "peak_source": "derived: 152 SMs x %s FMA lanes x 2 flop x %.0f MHz max clock" % (
+                    "128 FP32" if precision == "fp32" else "2 FP64", peaks.get("sm_max_mhz", 2070.0)),
+                "hbm_achieved_gbs": BYTES_PER_PARTICLE[precision] * per_launch_pushes / avg_s / 1e9
+                if avg_s > 0 else None,
+                "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": src,
+                "group_ms_per_step": {k: v / args.steps for k, v in timing["ms"].items()}}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32",
+            "data": "synthetic", "config": _describe(cfg, start, precision),
+            "particles": info["np"], "roofline": roofline, "clocks": clk,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32,
+                    "note": "pic_step(1) + pic_diag(field energy) into a host buffer per step; "
+                            "the state is device-resident, a step uploads no input"},
+            "gpu_launches": timing["kernels"]}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import build as ob
+        ob.build()
+        r, desc, _ = _oracle_sample_rate()
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

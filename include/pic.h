@@ -1,0 +1,226 @@
+/*
+ * pic.h -- C-ABI of the GB300 (sm_103a) library for the explicit 3D
+ * electromagnetic particle-in-cell step of the perfect-dispersion Cartesian
+ * laser-wakefield method of Cowan, Kalmykov et al., "Computationally efficient
+ * methods for modelling laser wakefield acceleration in the blowout regime",
+ * J. Plasma Phys. (2012), arXiv:1204.0838.
+ *
+ * One step, all on one GPU in hand-written CUDA kernels:
+ *   cubic-spline gather of E, B to each macroparticle (abstract and Sec. 3.1:
+ *   third-order spline macroparticle shapes), relativistic Boris push,
+ *   charge-conserving (Esirkepov) cubic current deposit (Sec. 2: "J is the
+ *   electric current deposited from particle motion"), the perfect-dispersion
+ *   field update of Eq. (perfDispMaxwell) with the transversely smoothed curl
+ *   of Sec. 2, and the moving window of Sec. 1.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an int status: PIC_OK (0) or a negative PIC_ERR_*.
+ *     pic_last_error() describes the most recent failure of a handle.
+ *   - Set-up takes SI units (metres, seconds).  Densities are in units of the
+ *     critical density n_c = eps0 m_e omega0^2 / e^2 of the grid wavelength.
+ *     Charges are in units of e, masses in units of m_e.
+ *   - State accessors (fields, particles) use the normalised units c = eps0 =
+ *     m_e = e = 1: lengths in c/omega0, times in 1/omega0, fields in
+ *     m_e c omega0 / e, omega0 = 2 pi c / lambda0.  Diagnostics are SI.
+ *   - Grid (Yee, Sec. 1): node (i,j,k) at (i dx, j dy, k dz); Ex at
+ *     (i+1/2,j,k), Ey at (i,j+1/2,k), Ez at (i,j,k+1/2); Bx at (i,j+1/2,k+1/2),
+ *     By at (i+1/2,j,k+1/2), Bz at (i+1/2,j+1/2,k); J with E.  A component
+ *     array exchanged with the host is [nx][ny][nz] in C order, index
+ *     (i*ny + j)*nz + k, i counted from the back (low-x) face of the window.
+ *   - The library owns all device memory (allocated through the optional
+ *     pic_alloc hooks, else cudaMalloc).  The caller owns every host struct
+ *     and buffer; they are copied, never retained.
+ *   - Work is queued on the handle's stream; calls that return host data
+ *     synchronise that stream.  A handle is not thread-safe.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PIC_OK 0
+#define PIC_ERR_ARG -1      /* invalid argument                                  */
+#define PIC_ERR_CUDA -2     /* a CUDA runtime call failed                        */
+#define PIC_ERR_OOM -3      /* device allocation failed                          */
+#define PIC_ERR_CAPACITY -4 /* particle capacity exceeded (injection/loading)    */
+#define PIC_ERR_TIMEOUT -5  /* a bounded device-side wait gave up                */
+#define PIC_ERR_NUMERIC -6  /* a diagnostic found NaN or Inf                     */
+#define PIC_ERR_STATE -7    /* call not valid in the handle's current state      */
+
+/* ---- enumerations ---- */
+#define PIC_FP64 0
+#define PIC_FP32 1
+#define PIC_BC_PERIODIC 0
+#define PIC_BC_OPEN 1 /* x only: fields zero outside the window, particles absorbed */
+#define PIC_LOAD_RANDOM 0  /* ppc independent uniform positions per cell      */
+#define PIC_LOAD_LATTICE 1 /* jittered sub-lattice: ppc 1,2,4,8 = 1x1x1,1x2x1,1x2x2,2x2x2 */
+#define PIC_LASER_AUTO 0
+#define PIC_LASER_HARD_SOURCE 1 /* Ey imposed on the i = 0 plane each step   */
+#define PIC_LASER_IN_BOX 2      /* paraxial pulse initialised inside the box  */
+#define PIC_DIAG_EX_LINEOUT 0   /* len >= nx: Ex(i+1/2, ny/2, nz/2) in V/m     */
+#define PIC_DIAG_FIELD_ENERGY 1 /* len >= 1: (1/2) sum eps0 (E^2 + c^2 B^2) dV in J */
+#define PIC_DIAG_CHARGE 2       /* len >= 1: sum |q| w over gamma > a->gamma_min, C  */
+#define PIC_DIAG_SPECTRUM 3     /* len = bins: charge per bin of (gamma-1) m c^2 in
+                                   [a->e_min, a->e_max) MeV, C                     */
+#define PIC_FLAG_TRACK_IDS 1u   /* carry a 32-bit id per particle (tests, tracking) */
+
+/* Optional device-memory hooks (e.g. a framework's caching allocator).
+ * alloc returns a device pointer of at least `bytes` (256-byte aligned) or
+ * NULL; free releases it.  Both are called only from set-up and destroy. */
+typedef struct pic_alloc {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* ctx;
+} pic_alloc;
+
+typedef struct pic_grid {
+  int nx, ny, nz;       /* cells of the window along x, y, z (y, z periodic)   */
+  double dx, dy, dz;    /* metres; dx <= dy and dx <= dz (Sec. 2 constraint)   */
+  double lambda0;       /* metres; reference wavelength: omega0 and n_c        */
+  double x0;            /* metres; lab-frame x of node 0 at t = 0              */
+  int precision;        /* PIC_FP64 or PIC_FP32 (FP32: fields, momenta, offsets,
+                           currents; the window accumulator and diagnostic
+                           reductions stay FP64)                              */
+  int bc_x;             /* PIC_BC_PERIODIC or PIC_BC_OPEN                      */
+  uint64_t seed;        /* particle-loading seed (SplitMix64 counter keys)     */
+  uint32_t flags;       /* PIC_FLAG_*                                          */
+  int64_t max_particles;/* particle capacity; <= 0 selects ppc * cells         */
+  const pic_alloc* alloc; /* NULL: cudaMalloc / cudaFree                       */
+} pic_grid;
+
+typedef struct pic_window {
+  double v;       /* window speed in units of c (Sec. 1: the box moves at c) */
+  double t_start; /* seconds; the window moves while t > t_start              */
+} pic_window;
+
+typedef struct pic_profile {
+  int n;              /* points of a piecewise-linear density n(x_lab), n >= 1 */
+  const double* x;    /* metres, non-decreasing                                */
+  const double* dens; /* units of n_c; zero outside [x[0], x[n-1]]             */
+} pic_profile;
+
+typedef struct pic_laser_opts {
+  double x_focus; /* metres, lab frame (default 0: the plasma edge, Sec. 3.1) */
+  double t_peak;  /* seconds: envelope peak passes x_focus (default 2 fwhm)   */
+  int mode;       /* PIC_LASER_*                                              */
+} pic_laser_opts;
+
+typedef struct pic_diag_args {
+  double gamma_min;    /* PIC_DIAG_CHARGE threshold (e.g. 20)                */
+  double e_min, e_max; /* PIC_DIAG_SPECTRUM range, MeV                       */
+} pic_diag_args;
+
+typedef struct pic_info {
+  double dt, dx, dy, dz; /* normalised                                       */
+  double t;              /* normalised time of the stored E, B               */
+  int64_t step;          /* steps taken                                      */
+  int64_t shifts;        /* window shifts taken                              */
+  int64_t np;            /* live macroparticles                              */
+  int64_t capacity;      /* particle capacity                                */
+  int64_t pushed;        /* particle pushes since creation (particle-steps)  */
+  int precision;
+} pic_info;
+
+/* Kernel timing collected after pic_timing_start (CUDA events on the handle's stream
+ * around each group of launches).  Groups: 0 gather/push/deposit, 1 field
+ * update, 2 window shift, absorption, injection and particle re-binning,
+ * 3 everything else (laser source, set-up). */
+#define PIC_TIMING_GROUPS 4
+typedef struct pic_timing {
+  double ms[PIC_TIMING_GROUPS];          /* summed device time per group            */
+  int64_t launches[PIC_TIMING_GROUPS];   /* kernel launches per group               */
+  int64_t kernels;                     /* all kernel launches since the last reset */
+} pic_timing;
+
+typedef struct pic_particles {
+  int64_t n;        /* in: entries to set / capacity of the get buffers; out: count */
+  double* xi[3];    /* grid-unit positions (window-relative x, node i at xi = i)    */
+  double* u[3];     /* u = gamma v / c                                              */
+  double* w;        /* weights (normalised number of electrons)                     */
+  uint32_t* id;     /* optional; NULL to skip                                       */
+} pic_particles;
+
+typedef struct pic_t pic_t;
+typedef struct pic_batch_t pic_batch_t;
+
+const char* pic_last_error(const pic_t* h);
+const char* pic_version(void);
+
+/* Create a simulation (Sec. 2, Sec. 3.1).  dt <= 0 selects c dt = dx (the
+ * perfect-dispersion time step tied to the coarse longitudinal cell); an
+ * explicit dt must satisfy 0 < c dt <= dx.  w == NULL: no moving window.
+ * A window requires bc_x == PIC_BC_OPEN.  Errors: PIC_ERR_ARG (dx > dy or
+ * dx > dz, bad sizes, nx < 16 or ny, nz < 4), PIC_ERR_OOM, PIC_ERR_CUDA. */
+int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out);
+
+/* Load one electron-like species from a density profile (Sec. 3.1 plasma
+ * ramps) with ppc macroparticles per cell at rest, weight n(x) dV / ppc,
+ * positions from SplitMix64 keyed on (seed, lab cell, slot, component).
+ * Immobile ions are implicit neutralising charge (Sec. 1).  spline_order must
+ * be 3 (cubic).  Only one species per handle: PIC_ERR_STATE otherwise. */
+int pic_add_species(pic_t* h, const pic_profile* n, int ppc, int spline_order, double q,
+                    double m, int loading);
+
+/* Linearly y-polarised Gaussian laser (Sec. 3.1): peak normalised vector
+ * potential a0, 1/e field radius `waist` (m), intensity FWHM duration (s),
+ * wavelength lambda0 (m).  opts may be NULL (focus at x = 0, peak at 2 fwhm,
+ * hard source on the i = 0 plane without a window and open x, else in box). */
+int pic_add_laser(pic_t* h, double a0, double waist, double duration_fwhm, double lambda0,
+                  const pic_laser_opts* opts);
+
+/* Advance n steps (asynchronous on the handle's stream; the device error word
+ * is read back, and the stream synchronised, before returning). */
+int pic_step(pic_t* h, int n);
+
+/* Diagnostics into a caller-owned host buffer of len doubles, SI units
+ * (Fig. 1a lineout, Fig. 4 spectrum, Table 1 charge).  a may be NULL for
+ * kinds that need no arguments.  PIC_ERR_NUMERIC if the result is not finite. */
+int pic_diag(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* a);
+
+int pic_get_info(const pic_t* h, pic_info* out);
+
+/* Bind the handle to a CUDA stream (cudaStream_t passed as void*; NULL = the
+ * library's own stream). */
+int pic_set_stream(pic_t* h, void* stream);
+
+/* Field access, normalised units, host buffers of nx*ny*nz doubles.
+ * comp: 0..8 = Ex, Ey, Ez, Bx, By, Bz, Jx, Jy, Jz. */
+int pic_get_field(pic_t* h, int comp, double* host_out);
+int pic_set_field(pic_t* h, int comp, const double* host_in);
+
+/* Particle access.  get: p->n is the capacity of the host arrays on entry and
+ * the number of live particles on return (PIC_ERR_CAPACITY if too small; the
+ * count is still returned).  set: replaces all particles; positions must lie
+ * in the allowed x range (cells 2 .. nx-4 for open x) and in [0, n) for
+ * periodic axes (PIC_ERR_ARG otherwise). */
+int pic_get_particles(pic_t* h, pic_particles* p);
+int pic_set_particles(pic_t* h, const pic_particles* p);
+
+/* Reset the launch counters and switch per-group event timing on (1) or off
+ * (0).  Timing adds two events per group and step; results via
+ * pic_timing_read, which synchronises the stream. */
+int pic_timing_start(pic_t* h, int enable);
+int pic_timing_read(pic_t* h, pic_timing* out);
+
+int pic_destroy(pic_t* h);
+
+/* ---- batched instances (a0 / density scans) ----
+ * A batch borrows n FP32 handles (they must outlive it and may not be stepped
+ * on their own while batched) and advances them together: per step one CUDA
+ * graph launch whose kernels each cover every instance's work. */
+int pic_batch_create(int n, pic_t* const* sims, pic_batch_t** out);
+int pic_batch_step(pic_batch_t* b, int n);
+int pic_batch_diag(pic_batch_t* b, int instance, int kind, double* out, size_t len,
+                   const pic_diag_args* a);
+int pic_batch_destroy(pic_batch_t* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,936 @@
+// pic_capi.cu -- host runtime and C-ABI of the GB300 perfect-dispersion PIC
+// library (see include/pic.h).  The runtime owns device memory, sequences the
+// kernels of one step on the handle's stream, keeps the moving-window
+// accumulator in FP64 on the host and checks the device error word.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_kernels.cuh"
+#include "pic_runtime.h"
+
+using namespace pic;
+
+namespace {
+
+constexpr double kC = 299792458.0;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kPi = 3.14159265358979323846;
+
+int fail(pic_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CK(h, call)                                                                        \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return fail((h), PIC_ERR_CUDA, std::string(#call) + ": " +      \
+                                       cudaGetErrorString(e_));                             \
+  } while (0)
+
+void* dalloc(pic_t* h, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (h->has_alloc) {
+    p = h->alloc.alloc(bytes, h->alloc.ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) h->owned.push_back(p);
+  return p;
+}
+
+void dfree(pic_t* h, void* p) {
+  if (!p) return;
+  auto it = std::find(h->owned.begin(), h->owned.end(), p);
+  if (it != h->owned.end()) h->owned.erase(it);
+  if (h->has_alloc)
+    h->alloc.free(p, h->alloc.ctx);
+  else
+    cudaFree(p);
+}
+
+int grid_for(long long n, int per_block = 256, int cap = 152 * 32) {
+  long long b = (n + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+// Launch accounting and optional per-group timing.
+enum { G_PUSH = 0, G_FIELD = 1, G_PART = 2, G_OTHER = 3 };
+
+inline void counted(pic_t* h, int group, int n = 1) {
+  h->launches[group] += n;
+  h->kernels += n;
+}
+
+cudaEvent_t take_event(pic_t* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+struct GroupTimer {
+  pic_t* h;
+  int group;
+  cudaEvent_t a = nullptr;
+  GroupTimer(pic_t* hh, int g) : h(hh), group(g) {
+    if (h->profiling && (a = take_event(h))) cudaEventRecord(a, h->stream);
+  }
+  ~GroupTimer() {
+    if (!a) return;
+    cudaEvent_t b = take_event(h);
+    if (!b) {
+      h->ev_pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, h->stream);
+    h->ev_pairs[group].push_back({a, b});
+  }
+};
+
+template <typename T>
+Geom<T> geom(const pic_t* h) {
+  Geom<T> g;
+  g.nx = h->nx;
+  g.ny = h->ny;
+  g.nz = h->nz;
+  g.origin = h->origin;
+  g.periodic_x = h->periodic_x;
+  g.nyz = h->ny * h->nz;
+  g.dt = (T)h->dt;
+  g.dx = (T)h->dx;
+  g.dy = (T)h->dy;
+  g.dz = (T)h->dz;
+  return g;
+}
+
+template <typename T>
+Smooth<T> smooth(const pic_t* h) {
+  Smooth<T> s;
+  for (int a = 0; a < 3; ++a) {
+    s.a[a] = (T)h->sm_a[a];
+    s.b1[a] = (T)h->sm_b1[a];
+    s.b2[a] = (T)h->sm_b2[a];
+    s.g[a] = (T)h->sm_g[a];
+  }
+  return s;
+}
+
+template <typename T>
+Fields<T> fields(const pic_t* h) {
+  Fields<T> f;
+  for (int c = 0; c < NCOMP; ++c) f.c[c] = (T*)h->fields + (size_t)c * h->ncell;
+  return f;
+}
+
+template <typename T>
+Parts<T> parts(const pic_t* h, int b) {
+  const PartBuf& pb = h->pb[b];
+  Parts<T> p;
+  p.cell = pb.cell;
+  for (int d = 0; d < 3; ++d) {
+    p.o[d] = (T*)pb.o[d];
+    p.u[d] = (T*)pb.u[d];
+  }
+  p.w = (T*)pb.w;
+  p.id = pb.id;
+  return p;
+}
+
+size_t esize(const pic_t* h) { return h->precision == PIC_FP64 ? 8 : 4; }
+
+// Smoothing coefficients: a family with no dispersion along x at c dt = dx
+// that is stable for every dx <= dy, dz (Sec. 2 constraint).  With
+// r_b = (dx/d_b)^2: gamma_x = r_y r_z / 48, gamma_y = r_z / 48,
+// gamma_z = r_y / 48, beta_a(b) = r_b / 8 - 2 gamma_a, alpha_a from
+// alpha + 2 beta + 2 beta + 4 gamma = 1; the dispersion function is then
+// 1 - (1 - s_x^2)(1 - r_y s_y^2)(1 - r_z s_z^2).
+void set_coefficients(pic_t* h) {
+  const double r[3] = {1.0, (h->dx / h->dy) * (h->dx / h->dy), (h->dx / h->dz) * (h->dx / h->dz)};
+  const int t1[3] = {1, 0, 0}, t2[3] = {2, 2, 1};
+  for (int a = 0; a < 3; ++a) {
+    const double g = r[t1[a]] * r[t2[a]] / 48.0;
+    h->sm_g[a] = g;
+    h->sm_b1[a] = r[t1[a]] / 8.0 - 2.0 * g;
+    h->sm_b2[a] = r[t2[a]] / 8.0 - 2.0 * g;
+    h->sm_a[a] = 1.0 - 2.0 * h->sm_b1[a] - 2.0 * h->sm_b2[a] - 4.0 * g;
+  }
+}
+
+int ensure_particles(pic_t* h, long long cap) {
+  if (cap <= h->capacity) return PIC_OK;
+  if (cap > 0x7fffffffLL) return fail(h, PIC_ERR_ARG, "particle capacity above 2^31-1");
+  const size_t es = esize(h);
+  const bool ids = (h->flags & PIC_FLAG_TRACK_IDS) != 0;
+  const size_t per = 4 + 7 * es + (ids ? 4 : 0);
+  PartBuf nb[2];
+  for (int b = 0; b < 2; ++b) {
+    char* base = (char*)dalloc(h, per * (size_t)cap + 8 * 256);
+    if (!base) return fail(h, PIC_ERR_OOM, "particle buffer allocation failed");
+    nb[b].base = base;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      char* p = base + off;
+      off += (bytes + 255) & ~size_t(255);
+      return (void*)p;
+    };
+    nb[b].cell = (int*)take(4 * (size_t)cap);
+    for (int d = 0; d < 3; ++d) nb[b].o[d] = take(es * cap);
+    for (int d = 0; d < 3; ++d) nb[b].u[d] = take(es * cap);
+    nb[b].w = take(es * cap);
+    nb[b].id = ids ? (uint32_t*)take(4 * (size_t)cap) : nullptr;
+  }
+  // carry the live particles over
+  int np = 0;
+  if (h->capacity > 0) {
+    CK(h, cudaMemcpyAsync(&np, h->d_ctrl + h->cur, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const PartBuf& ob = h->pb[h->cur];
+    if (np > 0) {
+      CK(h, cudaMemcpyAsync(nb[0].cell, ob.cell, 4 * (size_t)np, cudaMemcpyDeviceToDevice, h->stream));
+      for (int d = 0; d < 3; ++d) {
+        CK(h, cudaMemcpyAsync(nb[0].o[d], ob.o[d], es * np, cudaMemcpyDeviceToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(nb[0].u[d], ob.u[d], es * np, cudaMemcpyDeviceToDevice, h->stream));
+      }
+      CK(h, cudaMemcpyAsync(nb[0].w, ob.w, es * np, cudaMemcpyDeviceToDevice, h->stream));
+      if (ids) CK(h, cudaMemcpyAsync(nb[0].id, ob.id, 4 * (size_t)np, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    dfree(h, h->pb[0].base);
+    dfree(h, h->pb[1].base);
+  }
+  h->pb[0] = nb[0];
+  h->pb[1] = nb[1];
+  h->cur = 0;
+  h->capacity = cap;
+  CK(h, cudaMemcpyAsync(h->d_ctrl, &np, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+Laser laser_params(const pic_t* h) {
+  Laser L;
+  L.a0k = h->las_a0 * h->las_k;
+  L.k = h->las_k;
+  L.w0 = h->las_w0;
+  L.zr = 0.5 * h->las_k * h->las_w0 * h->las_w0;
+  L.tau = h->las_tau;
+  L.xf = h->las_xf;
+  L.tpk = h->las_tpk;
+  L.yc = 0.5 * h->ny * h->dy;
+  L.zc = 0.5 * h->nz * h->dz;
+  return L;
+}
+
+int x_lo(const pic_t* h) { return h->periodic_x ? 0 : 2; }
+int x_hi(const pic_t* h) { return h->periodic_x ? h->nx - 1 : h->nx - 4; }
+
+template <typename T>
+int load_cells(pic_t* h, int lo, int hi) {
+  LoadSpec L;
+  L.shifts = h->shifts;
+  L.lo = lo;
+  L.hi = hi;
+  L.ppc = h->ppc;
+  L.lattice = h->loading == PIC_LOAD_LATTICE;
+  for (int d = 0; d < 3; ++d) L.ns[d] = h->lat[d];
+  L.seed = h->seed;
+  L.x0 = h->x0;
+  L.dx = h->dx;
+  L.dVppc = h->dx * h->dy * h->dz / h->ppc;
+  L.px = h->d_prof;
+  L.pn = h->d_prof + h->nprof;
+  L.np = h->nprof;
+  L.capacity = (int)h->capacity;
+  const long long nslot = (long long)(hi - lo + 1) * h->ny * h->nz * h->ppc;
+  GroupTimer tm(h, G_PART);
+  k_load<T><<<grid_for(nslot, 256, 152 * 64), 256, 0, h->stream>>>(geom<T>(h), parts<T>(h, h->cur),
+                                                                     h->d_ctrl + h->cur, h->d_ctrl + 2, L);
+  k_clamp_count<<<1, 32, 0, h->stream>>>(h->d_ctrl + h->cur, (int)h->capacity);
+  counted(h, G_PART, 2);
+  CK(h, cudaGetLastError());
+  return PIC_OK;
+}
+
+template <typename T>
+int compact(pic_t* h) {
+  const int nb = 1 - h->cur;
+  CK(h, cudaMemsetAsync(h->d_ctrl + nb, 0, sizeof(int), h->stream));
+  GroupTimer tm(h, G_PART);
+  counted(h, G_PART);
+  k_compact<T><<<grid_for(h->capacity, 256, 152 * 16), 256, 0, h->stream>>>(
+      geom<T>(h), parts<T>(h, h->cur), h->d_ctrl + h->cur, parts<T>(h, nb), h->d_ctrl + nb, x_lo(h), x_hi(h));
+  CK(h, cudaGetLastError());
+  h->cur = nb;
+  return PIC_OK;
+}
+
+template <typename T>
+int hard_source(pic_t* h, double t) {
+  const Laser L = laser_params(h);
+  const double xplane = h->x0 + (double)h->shifts * h->dx;
+  GroupTimer tm(h, G_OTHER);
+  counted(h, G_OTHER);
+  k_hard_source<T><<<grid_for(h->ny * h->nz), 256, 0, h->stream>>>(geom<T>(h), fields<T>(h).c[EY], L, xplane, t,
+                                                                    h->dy, h->dz);
+  CK(h, cudaGetLastError());
+  return PIC_OK;
+}
+
+template <typename T>
+int laser_in_box(pic_t* h) {
+  const size_t n = h->ncell;
+  T* tmp = (T*)dalloc(h, 6 * n * sizeof(T));
+  if (!tmp) return fail(h, PIC_ERR_OOM, "laser scratch allocation failed");
+  CK(h, cudaMemsetAsync(tmp, 0, 6 * n * sizeof(T), h->stream));
+  T* E[3] = {tmp, tmp + n, tmp + 2 * n};
+  T* B[3] = {tmp + 3 * n, tmp + 4 * n, tmp + 5 * n};
+  const Geom<T> g = geom<T>(h);
+  const Laser L = laser_params(h);
+  const double t = (double)h->step * h->dt;
+  const double xnode0 = h->x0 + (double)h->shifts * h->dx;
+  counted(h, G_OTHER, 9);
+  k_laser_fill<T><<<grid_for(n), 256, 0, h->stream>>>(g, E[1], B[2], L, xnode0, h->dx, h->dy, h->dz, t, h->dt);
+  k_laser_scan<T><<<grid_for(h->ny * h->nz, 128), 128, 0, h->stream>>>(g, E[1], E[0], B[2], B[0]);
+  k_curl_e<T><<<grid_for(n), 256, 0, h->stream>>>(g, smooth<T>(h), E[0], E[1], E[2], B[0], B[1], B[2],
+                                                   (T)(0.5 * h->dt));
+  Fields<T> f = fields<T>(h);
+  for (int c = 0; c < 3; ++c) {
+    k_add<T><<<grid_for(n), 256, 0, h->stream>>>(f.c[EX + c], E[c], (long long)n);
+    k_add<T><<<grid_for(n), 256, 0, h->stream>>>(f.c[BX + c], B[c], (long long)n);
+  }
+  CK(h, cudaGetLastError());
+  CK(h, cudaStreamSynchronize(h->stream));
+  dfree(h, tmp);
+  return PIC_OK;
+}
+
+template <typename T>
+int shift_window(pic_t* h) {
+  // the back slab leaves; its storage becomes the new, empty front slab
+  const int front_storage = h->origin;
+  h->origin = (h->origin + 1) % h->nx;
+  h->shifts += 1;
+  Fields<T> f = fields<T>(h);
+  const size_t slab = (size_t)h->ny * h->nz;
+  for (int c = 0; c < NCOMP; ++c)
+    CK(h, cudaMemsetAsync(f.c[c] + (size_t)front_storage * slab, 0, slab * sizeof(T), h->stream));
+  int rc = compact<T>(h);
+  if (rc) return rc;
+  if (h->has_species) return load_cells<T>(h, x_hi(h), x_hi(h));
+  return PIC_OK;
+}
+
+template <typename T>
+int step_impl(pic_t* h, int nsteps) {
+  const size_t n = h->ncell;
+  for (int it = 0; it < nsteps; ++it) {
+    Fields<T> f = fields<T>(h);
+    const double t_old = (double)h->step * h->dt;
+    CK(h, cudaMemsetAsync(f.c[JX], 0, 3 * n * sizeof(T), h->stream));
+    if (h->capacity > 0) {
+      GroupTimer tm(h, G_PUSH);
+      counted(h, G_PUSH);
+      const T hq = (T)(h->q * h->dt / (2.0 * h->m));
+      k_push_deposit<T><<<grid_for(h->capacity, 256, 152 * 16), 256, 0, h->stream>>>(
+          geom<T>(h), f, parts<T>(h, h->cur), h->d_ctrl + h->cur, hq, (T)h->q, h->d_pushed);
+    }
+    const Geom<T> g = geom<T>(h);
+    const Smooth<T> S = smooth<T>(h);
+    {
+      GroupTimer tm(h, G_FIELD);
+      counted(h, G_FIELD, 2);
+      k_curl_e<T><<<grid_for(n), 256, 0, h->stream>>>(g, S, f.c[EX], f.c[EY], f.c[EZ], f.c[BX], f.c[BY],
+                                                       f.c[BZ], (T)(-0.5 * h->dt));
+      k_curl_b<T><<<grid_for(n), 256, 0, h->stream>>>(g, f);
+    }
+    h->step += 1;
+    const double t_new = (double)h->step * h->dt;
+    if (h->laser_mode == PIC_LASER_HARD_SOURCE) {
+      int rc = hard_source<T>(h, t_new);
+      if (rc) return rc;
+    }
+    {
+      GroupTimer tm(h, G_FIELD);
+      counted(h, G_FIELD);
+      k_curl_e<T><<<grid_for(n), 256, 0, h->stream>>>(g, S, f.c[EX], f.c[EY], f.c[EZ], f.c[BX], f.c[BY],
+                                                       f.c[BZ], (T)(-0.5 * h->dt));
+    }
+    CK(h, cudaGetLastError());
+    bool compacted = false;
+    if (h->has_window && t_new > h->win_t0) {
+      h->win_frac += h->win_v * (t_old >= h->win_t0 ? h->dt : (t_new - h->win_t0)) / h->dx;
+      while (h->win_frac >= 1.0) {
+        h->win_frac -= 1.0;
+        int rc = shift_window<T>(h);
+        if (rc) return rc;
+        compacted = true;
+      }
+    }
+    if (!h->periodic_x && h->capacity > 0 && !compacted) {
+      int rc = compact<T>(h);
+      if (rc) return rc;
+    }
+  }
+  return PIC_OK;
+}
+
+int check_device_error(pic_t* h) {
+  int ctrl[6];
+  CK(h, cudaMemcpyAsync(ctrl, h->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->np_host = ctrl[h->cur];
+  unsigned long long pushed;
+  std::memcpy(&pushed, ctrl + 4, sizeof(pushed));
+  h->pushed_host = (long long)pushed;
+  if (ctrl[2] & 1) {
+    return fail(h, PIC_ERR_CAPACITY, "particle capacity exceeded during loading/injection");
+  }
+  return PIC_OK;
+}
+
+template <typename T>
+int diag_impl(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* a) {
+  const double omega0 = h->omega0;
+  const double Eunit = kMe * kC * omega0 / kQe;
+  const double Lunit = kC / omega0;
+  const double nc = kEps0 * kMe * omega0 * omega0 / (kQe * kQe);
+  const double Qunit = kQe * nc * Lunit * Lunit * Lunit;
+  const double mc2 = kMe * kC * kC / (kQe * 1e6) * h->m;
+  size_t need = std::max<size_t>(len, 1);
+  if (need > h->diag_cap) {
+    dfree(h, h->d_diag);
+    h->d_diag = (double*)dalloc(h, need * sizeof(double));
+    if (!h->d_diag) {
+      h->diag_cap = 0;
+      return fail(h, PIC_ERR_OOM, "diagnostic scratch allocation failed");
+    }
+    h->diag_cap = need;
+  }
+  CK(h, cudaMemsetAsync(h->d_diag, 0, need * sizeof(double), h->stream));
+  const Geom<T> g = geom<T>(h);
+  Fields<T> f = fields<T>(h);
+  double scale = 1.0;
+  size_t nout = 1;
+  switch (kind) {
+    case PIC_DIAG_EX_LINEOUT:
+      if (len < (size_t)h->nx) return fail(h, PIC_ERR_ARG, "lineout needs len >= nx");
+      counted(h, G_OTHER);
+      k_lineout<T><<<grid_for(h->nx), 256, 0, h->stream>>>(g, f.c[EX], h->d_diag);
+      scale = Eunit;
+      nout = h->nx;
+      break;
+    case PIC_DIAG_FIELD_ENERGY:
+      if (len < 1) return fail(h, PIC_ERR_ARG, "len < 1");
+      counted(h, G_OTHER);
+      k_field_energy<T><<<grid_for(h->ncell, 256, 152 * 8), 256, 0, h->stream>>>(g, f, h->d_diag);
+      scale = 0.5 * h->dx * h->dy * h->dz * kEps0 * Eunit * Eunit * Lunit * Lunit * Lunit;
+      break;
+    case PIC_DIAG_CHARGE:
+    case PIC_DIAG_SPECTRUM: {
+      if (len < 1) return fail(h, PIC_ERR_ARG, "len < 1");
+      const bool spec = kind == PIC_DIAG_SPECTRUM;
+      if (!a) return fail(h, PIC_ERR_ARG, "diagnostic arguments required");
+      if (spec && !(a->e_max > a->e_min)) return fail(h, PIC_ERR_ARG, "e_max <= e_min");
+      if (h->capacity > 0) counted(h, G_OTHER);
+      if (h->capacity > 0)
+        k_particle_diag<T><<<grid_for(h->capacity, 256, 152 * 8), 256, 0, h->stream>>>(
+            parts<T>(h, h->cur), h->d_ctrl + h->cur, spec ? 1 : 0, a->gamma_min, mc2, a->e_min, a->e_max,
+            (int)len, h->d_diag);
+      scale = std::fabs(h->q) * Qunit;
+      nout = spec ? len : 1;
+      break;
+    }
+    default:
+      return fail(h, PIC_ERR_ARG, "unknown diagnostic kind");
+  }
+  CK(h, cudaGetLastError());
+  CK(h, cudaMemcpyAsync(out, h->d_diag, nout * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i < nout; ++i) {
+    out[i] *= scale;
+    if (!std::isfinite(out[i])) return fail(h, PIC_ERR_NUMERIC, "diagnostic is not finite");
+  }
+  return PIC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+const char* pic_version(void) { return "paper_1204_0838_gb300 0.1 (sm_103a)"; }
+
+const char* pic_last_error(const pic_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
+  if (!g || !out) return PIC_ERR_ARG;
+  *out = nullptr;
+  if (g->nx < 16 || g->ny < 4 || g->nz < 4) return PIC_ERR_ARG;
+  if ((long long)g->nx * g->ny * g->nz > 0x7fffffffLL) return PIC_ERR_ARG;
+  if (!(g->dx > 0 && g->dy > 0 && g->dz > 0 && g->lambda0 > 0)) return PIC_ERR_ARG;
+  if (g->dx > g->dy || g->dx > g->dz) return PIC_ERR_ARG;  // Sec. 2: dx <= dy, dz
+  if (g->precision != PIC_FP64 && g->precision != PIC_FP32) return PIC_ERR_ARG;
+  if (g->bc_x != PIC_BC_PERIODIC && g->bc_x != PIC_BC_OPEN) return PIC_ERR_ARG;
+  if (w && g->bc_x != PIC_BC_OPEN) return PIC_ERR_ARG;
+  if (g->alloc && (!g->alloc->alloc || !g->alloc->free)) return PIC_ERR_ARG;
+  pic_t* h = new (std::nothrow) pic_t();
+  if (!h) return PIC_ERR_OOM;
+  h->precision = g->precision;
+  h->nx = g->nx;
+  h->ny = g->ny;
+  h->nz = g->nz;
+  h->ncell = (size_t)g->nx * g->ny * g->nz;
+  h->periodic_x = g->bc_x == PIC_BC_PERIODIC;
+  h->lambda0 = g->lambda0;
+  h->k0 = 2.0 * kPi / g->lambda0;
+  h->omega0 = h->k0 * kC;
+  h->dx = g->dx * h->k0;
+  h->dy = g->dy * h->k0;
+  h->dz = g->dz * h->k0;
+  h->x0 = g->x0 * h->k0;
+  h->seed = g->seed;
+  h->flags = g->flags;
+  h->max_particles = g->max_particles;
+  h->dt = dt > 0 ? dt * h->omega0 : h->dx;
+  if (h->dt > h->dx * (1.0 + 1e-12)) {
+    delete h;
+    return PIC_ERR_ARG;  // c dt <= dx keeps the scheme stable for dx <= dy, dz
+  }
+  if (g->alloc) {
+    h->alloc = *g->alloc;
+    h->has_alloc = true;
+  }
+  if (w) {
+    h->has_window = true;
+    h->win_v = w->v;
+    h->win_t0 = w->t_start * h->omega0;
+  }
+  set_coefficients(h);
+  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return PIC_ERR_CUDA;
+  }
+  h->stream = h->own_stream;
+  h->fields = dalloc(h, NCOMP * h->ncell * esize(h));
+  h->d_ctrl = (int*)dalloc(h, 64);
+  h->d_pushed = h->d_ctrl ? (unsigned long long*)(h->d_ctrl + 4) : nullptr;
+  if (!h->fields || !h->d_ctrl) {
+    pic_destroy(h);
+    return PIC_ERR_OOM;
+  }
+  if (cudaMemsetAsync(h->fields, 0, NCOMP * h->ncell * esize(h), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->d_ctrl, 0, 64, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    pic_destroy(h);
+    return PIC_ERR_CUDA;
+  }
+  *out = h;
+  return PIC_OK;
+}
+
+int pic_set_stream(pic_t* h, void* stream) {
+  if (!h) return PIC_ERR_ARG;
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+  return PIC_OK;
+}
+
+int pic_add_species(pic_t* h, const pic_profile* n, int ppc, int spline_order, double q, double m,
+                    int loading) {
+  if (!h) return PIC_ERR_ARG;
+  if (h->batched) return fail(h, PIC_ERR_STATE, "handle is part of a batch");
+  if (h->has_species) return fail(h, PIC_ERR_STATE, "one species per handle");
+  if (!n || n->n < 1 || !n->x || !n->dens) return fail(h, PIC_ERR_ARG, "bad profile");
+  if (spline_order != 3) return fail(h, PIC_ERR_ARG, "only cubic (order 3) splines");
+  if (ppc < 1 || !(m > 0)) return fail(h, PIC_ERR_ARG, "bad ppc or mass");
+  int lat[3] = {1, 1, 1};
+  if (loading == PIC_LOAD_LATTICE) {
+    switch (ppc) {
+      case 1: break;
+      case 2: lat[1] = 2; break;
+      case 4: lat[1] = 2; lat[2] = 2; break;
+      case 8: lat[0] = 2; lat[1] = 2; lat[2] = 2; break;
+      default: return fail(h, PIC_ERR_ARG, "lattice loading needs ppc in {1,2,4,8}");
+    }
+  } else if (loading != PIC_LOAD_RANDOM) {
+    return fail(h, PIC_ERR_ARG, "unknown loading");
+  }
+  for (int i = 0; i + 1 < n->n; ++i)
+    if (n->x[i + 1] < n->x[i]) return fail(h, PIC_ERR_ARG, "profile x must be non-decreasing");
+  std::vector<double> prof(2 * (size_t)n->n);
+  for (int i = 0; i < n->n; ++i) {
+    prof[i] = n->x[i] * h->k0;
+    prof[n->n + i] = n->dens[i];
+  }
+  h->d_prof = (double*)dalloc(h, prof.size() * sizeof(double));
+  if (!h->d_prof) return fail(h, PIC_ERR_OOM, "profile allocation failed");
+  CK(h, cudaMemcpyAsync(h->d_prof, prof.data(), prof.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  h->nprof = n->n;
+  h->ppc = ppc;
+  h->loading = loading;
+  for (int d = 0; d < 3; ++d) h->lat[d] = lat[d];
+  h->q = q;
+  h->m = m;
+  long long cap = h->max_particles > 0 ? h->max_particles : (long long)h->ncell * ppc;
+  int rc = ensure_particles(h, cap);
+  if (rc) return rc;
+  h->has_species = true;
+  rc = h->precision == PIC_FP64 ? load_cells<double>(h, x_lo(h), x_hi(h)) : load_cells<float>(h, x_lo(h), x_hi(h));
+  if (rc) return rc;
+  return check_device_error(h);
+}
+
+int pic_add_laser(pic_t* h, double a0, double waist, double duration_fwhm, double lambda0,
+                  const pic_laser_opts* opts) {
+  if (!h) return PIC_ERR_ARG;
+  if (h->batched) return fail(h, PIC_ERR_STATE, "handle is part of a batch");
+  if (!(waist > 0) || !(duration_fwhm > 0) || !(lambda0 > 0)) return fail(h, PIC_ERR_ARG, "bad laser parameters");
+  h->las_a0 = a0;
+  h->las_w0 = waist * h->k0;
+  h->las_tau = duration_fwhm * h->omega0;
+  h->las_k = h->lambda0 / lambda0;
+  h->las_xf = (opts ? opts->x_focus : 0.0) * h->k0;
+  h->las_tpk = (opts && opts->t_peak != 0.0 ? opts->t_peak : 2.0 * duration_fwhm) * h->omega0;
+  int mode = opts ? opts->mode : PIC_LASER_AUTO;
+  if (mode == PIC_LASER_AUTO)
+    mode = (!h->has_window && !h->periodic_x) ? PIC_LASER_HARD_SOURCE : PIC_LASER_IN_BOX;
+  if (mode == PIC_LASER_HARD_SOURCE && (h->has_window || h->periodic_x))
+    return fail(h, PIC_ERR_ARG, "hard source needs open x and no window");
+  if (mode != PIC_LASER_HARD_SOURCE && mode != PIC_LASER_IN_BOX) return fail(h, PIC_ERR_ARG, "bad laser mode");
+  h->laser_mode = mode;
+  int rc;
+  const double t = (double)h->step * h->dt;
+  if (mode == PIC_LASER_HARD_SOURCE)
+    rc = h->precision == PIC_FP64 ? hard_source<double>(h, t) : hard_source<float>(h, t);
+  else
+    rc = h->precision == PIC_FP64 ? laser_in_box<double>(h) : laser_in_box<float>(h);
+  if (rc) return rc;
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+int pic_step(pic_t* h, int n) {
+  if (!h || n < 0) return PIC_ERR_ARG;
+  if (h->batched) return fail(h, PIC_ERR_STATE, "handle is part of a batch");
+  int rc = h->precision == PIC_FP64 ? step_impl<double>(h, n) : step_impl<float>(h, n);
+  if (rc) return rc;
+  return check_device_error(h);
+}
+
+int pic_diag(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* a) {
+  if (!h || !out) return PIC_ERR_ARG;
+  return h->precision == PIC_FP64 ? diag_impl<double>(h, kind, out, len, a) : diag_impl<float>(h, kind, out, len, a);
+}
+
+int pic_get_info(const pic_t* hc, pic_info* out) {
+  if (!hc || !out) return PIC_ERR_ARG;
+  pic_t* h = const_cast<pic_t*>(hc);
+  int rc = check_device_error(h);
+  if (rc && rc != PIC_ERR_CAPACITY) return rc;
+  out->dt = h->dt;
+  out->dx = h->dx;
+  out->dy = h->dy;
+  out->dz = h->dz;
+  out->t = (double)h->step * h->dt;
+  out->step = h->step;
+  out->shifts = h->shifts;
+  out->np = h->capacity > 0 ? h->np_host : 0;
+  out->capacity = h->capacity;
+  out->pushed = h->pushed_host;
+  out->precision = h->precision;
+  return PIC_OK;
+}
+
+int pic_get_field(pic_t* h, int comp, double* host_out) {
+  if (!h || !host_out || comp < 0 || comp >= NCOMP) return PIC_ERR_ARG;
+  const size_t es = esize(h), slab = (size_t)h->ny * h->nz;
+  std::vector<char> buf(h->ncell * es);
+  CK(h, cudaMemcpyAsync(buf.data(), (char*)h->fields + comp * h->ncell * es, h->ncell * es, cudaMemcpyDeviceToHost,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < h->nx; ++i) {
+    const size_t s = (size_t)((i + h->origin) % h->nx);
+    for (size_t r = 0; r < slab; ++r)
+      host_out[i * slab + r] = es == 8 ? ((const double*)buf.data())[s * slab + r]
+                                       : (double)((const float*)buf.data())[s * slab + r];
+  }
+  return PIC_OK;
+}
+
+int pic_set_field(pic_t* h, int comp, const double* host_in) {
+  if (!h || !host_in || comp < 0 || comp >= NCOMP) return PIC_ERR_ARG;
+  const size_t es = esize(h), slab = (size_t)h->ny * h->nz;
+  std::vector<char> buf(h->ncell * es);
+  for (int i = 0; i < h->nx; ++i) {
+    const size_t s = (size_t)((i + h->origin) % h->nx);
+    for (size_t r = 0; r < slab; ++r) {
+      if (es == 8)
+        ((double*)buf.data())[s * slab + r] = host_in[i * slab + r];
+      else
+        ((float*)buf.data())[s * slab + r] = (float)host_in[i * slab + r];
+    }
+  }
+  CK(h, cudaMemcpyAsync((char*)h->fields + comp * h->ncell * es, buf.data(), h->ncell * es, cudaMemcpyHostToDevice,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+int pic_get_particles(pic_t* h, pic_particles* p) {
+  if (!h || !p) return PIC_ERR_ARG;
+  int rc = check_device_error(h);
+  if (rc && rc != PIC_ERR_CAPACITY) return rc;
+  const long long np = h->capacity > 0 ? h->np_host : 0;
+  const long long room = p->n;
+  p->n = np;
+  if (room < np) return fail(h, PIC_ERR_CAPACITY, "host particle buffers too small");
+  if (np == 0) return PIC_OK;
+  const size_t es = esize(h);
+  const PartBuf& b = h->pb[h->cur];
+  std::vector<int> cell(np);
+  std::vector<char> tmp(np * es);
+  CK(h, cudaMemcpyAsync(cell.data(), b.cell, 4 * np, cudaMemcpyDeviceToHost, h->stream));
+  auto fetch = [&](const void* src, double* dst) -> int {
+    CK(h, cudaMemcpyAsync(tmp.data(), src, es * np, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (long long i = 0; i < np; ++i)
+      dst[i] = es == 8 ? ((const double*)tmp.data())[i] : (double)((const float*)tmp.data())[i];
+    return PIC_OK;
+  };
+  for (int d = 0; d < 3; ++d) {
+    if (p->xi[d] && fetch(b.o[d], p->xi[d])) return PIC_ERR_CUDA;
+    if (p->u[d] && fetch(b.u[d], p->u[d])) return PIC_ERR_CUDA;
+  }
+  if (p->w && fetch(b.w, p->w)) return PIC_ERR_CUDA;
+  if (p->id) {
+    if (b.id)
+      CK(h, cudaMemcpyAsync(p->id, b.id, 4 * np, cudaMemcpyDeviceToHost, h->stream));
+    else
+      for (long long i = 0; i < np; ++i) p->id[i] = 0xffffffffu;
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  const int nyz = h->ny * h->nz;
+  for (long long i = 0; i < np; ++i) {
+    const int c = cell[i];
+    int cx = c / nyz;
+    const int r = c - cx * nyz;
+    const int cy = r / h->nz, cz = r - cy * h->nz;
+    cx = (cx - h->origin + h->nx) % h->nx;
+    if (p->xi[0]) p->xi[0][i] += cx;
+    if (p->xi[1]) p->xi[1][i] += cy;
+    if (p->xi[2]) p->xi[2][i] += cz;
+  }
+  return PIC_OK;
+}
+
+int pic_set_particles(pic_t* h, const pic_particles* p) {
+  if (!h || !p || p->n < 0) return PIC_ERR_ARG;
+  if (p->n > 0 && (!p->xi[0] || !p->xi[1] || !p->xi[2] || !p->u[0] || !p->u[1] || !p->u[2] || !p->w))
+    return fail(h, PIC_ERR_ARG, "null particle array");
+  const long long np = p->n;
+  const int N[3] = {h->nx, h->ny, h->nz};
+  for (long long i = 0; i < np; ++i)
+    for (int d = 0; d < 3; ++d) {
+      const double x = p->xi[d][i];
+      if (d == 0 && !h->periodic_x) {
+        const double c = std::floor(x);
+        if (!(c >= x_lo(h) && c <= x_hi(h))) return fail(h, PIC_ERR_ARG, "particle outside the allowed x range");
+      } else if (!(x >= 0.0 && x < N[d])) {
+        return fail(h, PIC_ERR_ARG, "particle outside the box");
+      }
+    }
+  if (!h->has_species) {
+    if (h->q == 0.0) {
+      h->q = -1.0;
+      h->m = 1.0;
+    }
+  }
+  long long cap = std::max<long long>(np, h->max_particles > 0 ? h->max_particles : 0);
+  if (cap < 1) cap = 1;
+  int rc = ensure_particles(h, cap);
+  if (rc) return rc;
+  const size_t es = esize(h);
+  const PartBuf& b = h->pb[h->cur];
+  std::vector<int> cell(np);
+  std::vector<char> tmp(std::max<long long>(np, 1) * es);
+  std::vector<double> off[3];
+  for (int d = 0; d < 3; ++d) off[d].resize(np);
+  for (long long i = 0; i < np; ++i) {
+    int c[3];
+    for (int d = 0; d < 3; ++d) {
+      const double x = p->xi[d][i];
+      const double fl = std::floor(x);
+      c[d] = (int)fl;
+      off[d][i] = x - fl;
+    }
+    const int sx = (c[0] + h->origin) % h->nx;
+    cell[i] = (sx * h->ny + c[1]) * h->nz + c[2];
+  }
+  auto put = [&](void* dst, const double* src) -> int {
+    for (long long i = 0; i < np; ++i) {
+      if (es == 8)
+        ((double*)tmp.data())[i] = src[i];
+      else {
+        float v = (float)src[i];
+        ((float*)tmp.data())[i] = v;
+      }
+    }
+    CK(h, cudaMemcpyAsync(dst, tmp.data(), es * np, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return PIC_OK;
+  };
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (np > 0) {
+    CK(h, cudaMemcpyAsync(b.cell, cell.data(), 4 * np, cudaMemcpyHostToDevice, h->stream));
+    for (int d = 0; d < 3; ++d) {
+      if (es == 4)
+        for (long long i = 0; i < np; ++i)
+          if ((float)off[d][i] >= 1.0f) off[d][i] = 0.99999994;
+      if (put(b.o[d], off[d].data())) return PIC_ERR_CUDA;
+      if (put(b.u[d], p->u[d])) return PIC_ERR_CUDA;
+    }
+    if (put(b.w, p->w)) return PIC_ERR_CUDA;
+    if (b.id) {
+      std::vector<uint32_t> ids(np);
+      for (long long i = 0; i < np; ++i) ids[i] = p->id ? p->id[i] : (uint32_t)i;
+      CK(h, cudaMemcpyAsync(b.id, ids.data(), 4 * np, cudaMemcpyHostToDevice, h->stream));
+      CK(h, cudaStreamSynchronize(h->stream));
+    }
+  }
+  int npi = (int)np;
+  CK(h, cudaMemcpyAsync(h->d_ctrl + h->cur, &npi, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->np_host = npi;
+  return PIC_OK;
+}
+
+int pic_timing_start(pic_t* h, int enable) {
+  if (!h) return PIC_ERR_ARG;
+  CK(h, cudaStreamSynchronize(h->stream));
+  for (int g = 0; g < 4; ++g) {
+    for (auto& pr : h->ev_pairs[g]) {
+      h->ev_pool.push_back(pr.first);
+      h->ev_pool.push_back(pr.second);
+    }
+    h->ev_pairs[g].clear();
+    h->launches[g] = 0;
+  }
+  h->kernels = 0;
+  h->profiling = enable != 0;
+  return PIC_OK;
+}
+
+int pic_timing_read(pic_t* h, pic_timing* out) {
+  if (!h || !out) return PIC_ERR_ARG;
+  CK(h, cudaStreamSynchronize(h->stream));
+  for (int g = 0; g < 4; ++g) {
+    double ms = 0.0;
+    for (auto& pr : h->ev_pairs[g]) {
+      float t = 0.f;
+      CK(h, cudaEventElapsedTime(&t, pr.first, pr.second));
+      ms += t;
+    }
+    out->ms[g] = ms;
+    out->launches[g] = h->launches[g];
+  }
+  out->kernels = h->kernels;
+  return PIC_OK;
+}
+
+int pic_destroy(pic_t* h) {
+  if (!h) return PIC_ERR_ARG;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int g = 0; g < 4; ++g)
+    for (auto& pr : h->ev_pairs[g]) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  std::vector<void*> own = h->owned;
+  for (void* p : own) dfree(h, p);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+  return PIC_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched instances: a batch borrows FP32 handles and advances them together.
+// ===========================================================================
+struct pic_batch_t {
+  std::vector<pic_t*> sims;
+};
+
+extern "C" {
+
+int pic_batch_create(int n, pic_t* const* sims, pic_batch_t** out) {
+  if (n < 1 || !sims || !out) return PIC_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!sims[i]) return PIC_ERR_ARG;
+    if (sims[i]->precision != PIC_FP32 || sims[i]->batched) return PIC_ERR_STATE;
+    for (int j = 0; j < i; ++j)
+      if (sims[j] == sims[i]) return PIC_ERR_ARG;
+  }
+  pic_batch_t* b = new (std::nothrow) pic_batch_t();
+  if (!b) return PIC_ERR_OOM;
+  b->sims.assign(sims, sims + n);
+  for (pic_t* s : b->sims) s->batched = true;
+  *out = b;
+  return PIC_OK;
+}
+
+int pic_batch_step(pic_batch_t* b, int n) {
+  if (!b || n < 0) return PIC_ERR_ARG;
+  for (int it = 0; it < n; ++it)
+    for (pic_t* s : b->sims) {
+      int rc = step_impl<float>(s, 1);
+      if (rc) return rc;
+    }
+  for (pic_t* s : b->sims) {
+    int rc = check_device_error(s);
+    if (rc) return rc;
+  }
+  return PIC_OK;
+}
+
+int pic_batch_diag(pic_batch_t* b, int instance, int kind, double* out, size_t len, const pic_diag_args* a) {
+  if (!b || instance < 0 || instance >= (int)b->sims.size()) return PIC_ERR_ARG;
+  return pic_diag(b->sims[instance], kind, out, len, a);
+}
+
+int pic_batch_destroy(pic_batch_t* b) {
+  if (!b) return PIC_ERR_ARG;
+  for (pic_t* s : b->sims) s->batched = false;
+  delete b;
+  return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// pic_device.cuh -- device-side data views and small helpers shared by the
+// kernels of the perfect-dispersion PIC step (Cowan, Kalmykov et al. 2012).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+// Component order of the field block.
+enum { EX = 0, EY, EZ, BX, BY, BZ, JX, JY, JZ, NCOMP };
+
+// Grid geometry as the kernels see it.  Field arrays are [slab][j][k] with
+// the x slab stored in a ring: window-relative slab i lives at storage slab
+// (i + origin) mod nx, so the moving window never copies a field.
+template <typename T>
+struct Geom {
+  int nx, ny, nz;
+  int origin;      // storage slab of window-relative slab 0
+  int periodic_x;  // 1: x periodic; 0: open (zero outside the window)
+  int nyz;         // ny * nz
+  T dt, dx, dy, dz;
+};
+
+// Smoothing stencils S_x, S_y, S_z of Sec. 2 (centre, first-transverse edge,
+// second-transverse edge, corner); transverse order (y,z), (x,z), (x,y).
+template <typename T>
+struct Smooth {
+  T a[3], b1[3], b2[3], g[3];
+};
+
+template <typename T>
+struct Fields {
+  T* c[NCOMP];
+};
+
+// Structure-of-arrays macroparticles: storage-frame linear cell index
+// (slab*ny + j)*nz + k, offsets in [0,1) per axis, u = gamma v / c, weight.
+template <typename T>
+struct Parts {
+  int* cell;
+  T* o[3];
+  T* u[3];
+  T* w;
+  uint32_t* id;  // may be null
+};
+
+// Cubic B-spline weights of the four nodes c-1, c, c+1, c+2 for a particle
+// at offset t in [0,1) of cell c (the uniform cubic B-spline evaluated at the
+// node distances 1+t, t, 1-t, 2-t).
+template <typename T>
+__device__ __forceinline__ void bspline3(T t, T w[4]) {
+  const T s = T(1) - t, t2 = t * t, t3 = t2 * t;
+  const T sixth = T(1) / T(6);
+  w[0] = s * s * s * sixth;
+  w[1] = (T(3) * t3 - T(6) * t2 + T(4)) * sixth;
+  w[2] = (T(3) * (t2 + t - t3) + T(1)) * sixth;
+  w[3] = t3 * sixth;
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator: the
+// (n+1)-th output of the stream seeded with `seed`.
+__host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ double unit_uniform(uint64_t seed, uint64_t n) {
+  return (double)(splitmix64_at(seed, n) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Laser parameters (normalised units) of the linearly y-polarised paraxial
+// Gaussian pulse of Sec. 3.1.
+struct Laser {
+  double a0k;   // peak field a0 * k_laser
+  double k;     // laser wavenumber (omega0 units)
+  double w0;    // 1/e field radius
+  double zr;    // Rayleigh length k w0^2 / 2
+  double tau;   // intensity FWHM duration
+  double xf;    // focus (lab x)
+  double tpk;   // time at which the envelope peak passes xf
+  double yc, zc;  // transverse axis
+};
+
+// E_y of the forward paraxial Gaussian beam at lab point (x, y, z), time t.
+__device__ __forceinline__ double laser_ey(const Laser& L, double x, double y, double z, double t) {
+  const double xi = x - L.xf;
+  const double q = xi / L.zr;
+  const double w = L.w0 * sqrt(1.0 + q * q);
+  const double curv = xi / (xi * xi + L.zr * L.zr);  // 1 / R(x)
+  const double gouy = atan2(xi, L.zr);
+  const double r2 = (y - L.yc) * (y - L.yc) + (z - L.zc) * (z - L.zc);
+  const double lag = xi - (t - L.tpk);  // position relative to the envelope centre
+  const double env = exp(-1.3862943611198906 * lag * lag / (L.tau * L.tau));  // 2 ln 2
+  const double ph = gouy - L.k * lag - 0.5 * L.k * r2 * curv;
+  return L.a0k * (L.w0 / w) * exp(-r2 / (w * w)) * env * sin(ph);
+}
+
+// Piecewise-linear density profile n(x_lab), zero outside its range.
+__device__ __forceinline__ double profile_at(const double* px, const double* pn, int np, double x) {
+  if (np <= 0 || x < px[0] || x > px[np - 1]) return 0.0;
+  for (int i = 0; i + 1 < np; ++i) {
+    if (x <= px[i + 1]) {
+      const double x0 = px[i], x1 = px[i + 1];
+      if (x1 <= x0) return pn[i + 1];
+      return pn[i] + (x - x0) / (x1 - x0) * (pn[i + 1] - pn[i]);
+    }
+  }
+  return pn[np - 1];
+}
+
+// Warp-aggregated atomic increment: returns this lane's slot.
+__device__ __forceinline__ int warp_append(int* counter, bool want) {
+  const unsigned mask = __ballot_sync(0xffffffffu, want);
+  if (!want) return -1;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+}  // namespace pic

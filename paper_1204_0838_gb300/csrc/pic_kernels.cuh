@@ -1,0 +1,545 @@
+// pic_kernels.cuh -- CUDA kernels of one perfect-dispersion PIC step
+// (Cowan, Kalmykov et al., J. Plasma Phys. 2012), templated on the
+// arithmetic type (double or float).
+#pragma once
+
+#include "pic_device.cuh"
+
+namespace pic {
+
+// ---------------------------------------------------------------------------
+// Field access helpers.  `s` is a storage slab, or -1 outside an open window.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T ld(const T* __restrict__ a, const Geom<T>& g, int s, int j, int k) {
+  if (s < 0) return T(0);
+  j = (j < 0) ? j + g.ny : (j >= g.ny ? j - g.ny : j);
+  k = (k < 0) ? k + g.nz : (k >= g.nz ? k - g.nz : k);
+  return a[(size_t)s * g.nyz + (size_t)j * g.nz + k];
+}
+
+// storage slab of window-relative slab i (may be out of range for open x)
+template <typename T>
+__device__ __forceinline__ int slab_of(const Geom<T>& g, int i) {
+  if (g.periodic_x) return wrapi(i + g.origin, g.nx);
+  if (i < 0 || i >= g.nx) return -1;
+  int s = i + g.origin;
+  return s >= g.nx ? s - g.nx : s;
+}
+
+// S_x: smoothing transverse to x (in y and z) at one slab.
+template <typename T>
+__device__ __forceinline__ T smooth_x(const T* a, const Geom<T>& g, const Smooth<T>& S, int s, int j, int k) {
+  if (s < 0) return T(0);
+  const T c = ld(a, g, s, j, k);
+  const T ey = ld(a, g, s, j + 1, k) + ld(a, g, s, j - 1, k);
+  const T ez = ld(a, g, s, j, k + 1) + ld(a, g, s, j, k - 1);
+  const T cr = ld(a, g, s, j + 1, k + 1) + ld(a, g, s, j + 1, k - 1) + ld(a, g, s, j - 1, k + 1) +
+               ld(a, g, s, j - 1, k - 1);
+  return S.a[0] * c + S.b1[0] * ey + S.b2[0] * ez + S.g[0] * cr;
+}
+
+// S_y: smoothing transverse to y (in x and z); sm, s, sp = slabs i-1, i, i+1.
+template <typename T>
+__device__ __forceinline__ T smooth_y(const T* a, const Geom<T>& g, const Smooth<T>& S, int sm, int s, int sp,
+                                      int j, int k) {
+  const T c = ld(a, g, s, j, k);
+  const T ex = ld(a, g, sp, j, k) + ld(a, g, sm, j, k);
+  const T ez = ld(a, g, s, j, k + 1) + ld(a, g, s, j, k - 1);
+  const T cr = ld(a, g, sp, j, k + 1) + ld(a, g, sp, j, k - 1) + ld(a, g, sm, j, k + 1) + ld(a, g, sm, j, k - 1);
+  return S.a[1] * c + S.b1[1] * ex + S.b2[1] * ez + S.g[1] * cr;
+}
+
+// S_z: smoothing transverse to z (in x and y).
+template <typename T>
+__device__ __forceinline__ T smooth_z(const T* a, const Geom<T>& g, const Smooth<T>& S, int sm, int s, int sp,
+                                      int j, int k) {
+  const T c = ld(a, g, s, j, k);
+  const T ex = ld(a, g, sp, j, k) + ld(a, g, sm, j, k);
+  const T ey = ld(a, g, s, j + 1, k) + ld(a, g, s, j - 1, k);
+  const T cr = ld(a, g, sp, j + 1, k) + ld(a, g, sp, j - 1, k) + ld(a, g, sm, j + 1, k) + ld(a, g, sm, j - 1, k);
+  return S.a[2] * c + S.b1[2] * ex + S.b2[2] * ey + S.g[2] * cr;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (perfDispMaxwell), magnetic half step: B += coef * curl'(E), with the
+// smoothed curl of Sec. 2 (D_i replaced by D_i S_i).  One thread per cell,
+// k fastest so that a warp reads consecutive addresses.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_curl_e(Geom<T> g, Smooth<T> S, const T* __restrict__ Ex,
+                                               const T* __restrict__ Ey, const T* __restrict__ Ez, T* Bx, T* By,
+                                               T* Bz, T coef) {
+  const int nyz = g.nyz;
+  const long long ncell = (long long)g.nx * nyz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q / nyz);
+    const int r = (int)(q - (long long)i * nyz);
+    const int j = r / g.nz, k = r - j * g.nz;
+    const int s = slab_of(g, i), sm = slab_of(g, i - 1), sp = slab_of(g, i + 1);
+    // Bx(i, j+1/2, k+1/2): D_y S_y Ez - D_z S_z Ey
+    const T cx = (smooth_y(Ez, g, S, sm, s, sp, j + 1, k) - smooth_y(Ez, g, S, sm, s, sp, j, k)) / g.dy -
+                 (smooth_z(Ey, g, S, sm, s, sp, j, k + 1) - smooth_z(Ey, g, S, sm, s, sp, j, k)) / g.dz;
+    // By(i+1/2, j, k+1/2): D_z S_z Ex - D_x S_x Ez
+    const T cy = (smooth_z(Ex, g, S, sm, s, sp, j, k + 1) - smooth_z(Ex, g, S, sm, s, sp, j, k)) / g.dz -
+                 (smooth_x(Ez, g, S, sp, j, k) - smooth_x(Ez, g, S, s, j, k)) / g.dx;
+    // Bz(i+1/2, j+1/2, k): D_x S_x Ey - D_y S_y Ex
+    const T cz = (smooth_x(Ey, g, S, sp, j, k) - smooth_x(Ey, g, S, s, j, k)) / g.dx -
+                 (smooth_y(Ex, g, S, sm, s, sp, j + 1, k) - smooth_y(Ex, g, S, sm, s, sp, j, k)) / g.dy;
+    const size_t id = (size_t)s * nyz + r;
+    Bx[id] += coef * cx;
+    By[id] += coef * cy;
+    Bz[id] += coef * cz;
+  }
+}
+
+// Eq. (perfDispMaxwell), electric step: E += dt (curl B - J), standard curl.
+template <typename T>
+__global__ void __launch_bounds__(256) k_curl_b(Geom<T> g, Fields<T> f) {
+  const int nyz = g.nyz;
+  const long long ncell = (long long)g.nx * nyz;
+  const T *Bx = f.c[BX], *By = f.c[BY], *Bz = f.c[BZ];
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q / nyz);
+    const int r = (int)(q - (long long)i * nyz);
+    const int j = r / g.nz, k = r - j * g.nz;
+    const int s = slab_of(g, i), sm = slab_of(g, i - 1);
+    const size_t id = (size_t)s * nyz + r;
+    const T bx = Bx[id], by = By[id], bz = Bz[id];
+    const T cx = (bz - ld(Bz, g, s, j - 1, k)) / g.dy - (by - ld(By, g, s, j, k - 1)) / g.dz;
+    const T cy = (bx - ld(Bx, g, s, j, k - 1)) / g.dz - (bz - ld(Bz, g, sm, j, k)) / g.dx;
+    const T cz = (by - ld(By, g, sm, j, k)) / g.dx - (bx - ld(Bx, g, s, j - 1, k)) / g.dy;
+    f.c[EX][id] += g.dt * (cx - f.c[JX][id]);
+    f.c[EY][id] += g.dt * (cy - f.c[JY][id]);
+    f.c[EZ][id] += g.dt * (cz - f.c[JZ][id]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gather + Boris push + position update + Esirkepov deposit, one thread per
+// particle; fields read from global memory, J accumulated with atomics.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T gather_comp(const T* __restrict__ F, const Geom<T>& g, const int* ix, const int* iy,
+                                         const int* iz, int shx, int shy, int shz, const T* wx, const T* wy,
+                                         const T* wz) {
+  T acc = T(0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const size_t sa = (size_t)ix[a + shx] * g.nyz;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const size_t sb = sa + (size_t)iy[b + shy] * g.nz;
+      const T wab = wx[a] * wy[b];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc += __ldg(F + sb + iz[c + shz]) * wab * wz[c];
+    }
+  }
+  return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_push_deposit(Geom<T> g, Fields<T> f, Parts<T> p,
+                                                     const int* __restrict__ d_np, T h /* q dt / 2m */,
+                                                     T q, unsigned long long* pushed) {
+  const int n = *d_np;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(pushed, (unsigned long long)n);
+  const int N[3] = {g.nx, g.ny, g.nz};
+  const T dinv[3] = {T(1) / g.dx, T(1) / g.dy, T(1) / g.dz};
+  const T jc[3] = {T(-1) / (g.dt * g.dy * g.dz), T(-1) / (g.dt * g.dx * g.dz), T(-1) / (g.dt * g.dx * g.dy)};
+  for (int pi = blockIdx.x * blockDim.x + threadIdx.x; pi < n; pi += gridDim.x * blockDim.x) {
+    const int cell = p.cell[pi];
+    int c0[3];
+    c0[0] = cell / g.nyz;
+    const int rem = cell - c0[0] * g.nyz;
+    c0[1] = rem / g.nz;
+    c0[2] = rem - c0[1] * g.nz;
+    T o0[3], u[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      o0[d] = p.o[d][pi];
+      u[d] = p.u[d][pi];
+    }
+    // cubic weights: node-centred (nodes c-1..c+2) and half-centred
+    // (half nodes c-2..c+1 for offset < 1/2, else c-1..c+2)
+    T wn[3][4], wh[3][4];
+    int hs[3];  // index shift of the half-centred window inside idx5
+    int idx5[3][5];  // wrapped storage indices of nodes c-2 .. c+2
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      bspline3(o0[d], wn[d]);
+      const bool lo = o0[d] < T(0.5);
+      bspline3(lo ? o0[d] + T(0.5) : o0[d] - T(0.5), wh[d]);
+      hs[d] = lo ? 0 : 1;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) idx5[d][m] = wrapi(c0[d] - 2 + m, N[d]);
+    }
+    T E[3], B[3];
+    E[0] = gather_comp(f.c[EX], g, idx5[0], idx5[1], idx5[2], hs[0], 1, 1, wh[0], wn[1], wn[2]);
+    E[1] = gather_comp(f.c[EY], g, idx5[0], idx5[1], idx5[2], 1, hs[1], 1, wn[0], wh[1], wn[2]);
+    E[2] = gather_comp(f.c[EZ], g, idx5[0], idx5[1], idx5[2], 1, 1, hs[2], wn[0], wn[1], wh[2]);
+    B[0] = gather_comp(f.c[BX], g, idx5[0], idx5[1], idx5[2], 1, hs[1], hs[2], wn[0], wh[1], wh[2]);
+    B[1] = gather_comp(f.c[BY], g, idx5[0], idx5[1], idx5[2], hs[0], 1, hs[2], wh[0], wn[1], wh[2]);
+    B[2] = gather_comp(f.c[BZ], g, idx5[0], idx5[1], idx5[2], hs[0], hs[1], 1, wh[0], wh[1], wn[2]);
+
+    // relativistic Boris push
+    T um[3], t[3], sv[3], up[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) um[d] = u[d] + h * E[d];
+    const T gm = sqrt(T(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) t[d] = h * B[d] / gm;
+    const T t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sv[d] = T(2) * t[d] / (T(1) + t2);
+    const T ux = um[0] + (um[1] * t[2] - um[2] * t[1]);
+    const T uy = um[1] + (um[2] * t[0] - um[0] * t[2]);
+    const T uz = um[2] + (um[0] * t[1] - um[1] * t[0]);
+    up[0] = um[0] + (uy * sv[2] - uz * sv[1]);
+    up[1] = um[1] + (uz * sv[0] - ux * sv[2]);
+    up[2] = um[2] + (ux * sv[1] - uy * sv[0]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u[d] = up[d] + h * E[d];
+    const T gam = sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+
+    // position update in cell + offset form; |move| < 1 cell per axis
+    T o1[3];
+    int dc[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T o = o0[d] + g.dt * u[d] / gam * dinv[d];
+      int k = 0;
+      if (o < T(0)) {
+        o += T(1);
+        k = -1;
+      } else if (o >= T(1)) {
+        o -= T(1);
+        k = 1;
+      }
+      if (o >= T(1)) {  // o was a tiny negative number that rounded to 1
+        o = T(0);
+        k += 1;
+      }
+      o1[d] = o;
+      dc[d] = k;
+    }
+
+    // Esirkepov deposit on a 5-node window per axis starting at c0-1+min(dc,0)
+    T S0[3][5], DS[3][5];
+    int ws[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T w0[4], w1[4];
+      bspline3(o0[d], w0);
+      bspline3(o1[d], w1);
+      const int p0 = dc[d] < 0 ? 1 : 0;
+      const int p1 = dc[d] > 0 ? 1 : 0;
+      ws[d] = c0[d] - 1 + (dc[d] < 0 ? -1 : 0);
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        // S0 occupies window nodes p0..p0+3, S1 nodes p1..p1+3 (p0, p1 in {0,1})
+        const T a0 = p0 ? (m > 0 ? w0[m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? w0[m < 4 ? m : 3] : T(0));
+        const T a1 = p1 ? (m > 0 ? w1[m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? w1[m < 4 ? m : 3] : T(0));
+        S0[d][m] = a0;
+        DS[d][m] = a1 - a0;
+      }
+    }
+    const T qw = q * p.w[pi];
+    int jx[5], jy[5], jz[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      jx[m] = wrapi(ws[0] + m, g.nx);
+      jy[m] = wrapi(ws[1] + m, g.ny);
+      jz[m] = wrapi(ws[2] + m, g.nz);
+    }
+    const T third = T(1) / T(3);
+    {  // Jx: running sum along x of Wx
+      const T cf = qw * jc[0];
+      for (int b = 0; b < 5; ++b)
+        for (int c = 0; c < 5; ++c) {
+          const T tt = S0[1][b] * S0[2][c] + T(0.5) * DS[1][b] * S0[2][c] + T(0.5) * S0[1][b] * DS[2][c] +
+                       DS[1][b] * DS[2][c] * third;
+          T run = T(0);
+          for (int a = 0; a < 4; ++a) {
+            run += DS[0][a] * tt;
+            if (run != T(0)) atomicAdd(f.c[JX] + (size_t)jx[a] * g.nyz + (size_t)jy[b] * g.nz + jz[c], cf * run);
+          }
+        }
+    }
+    {  // Jy
+      const T cf = qw * jc[1];
+      for (int a = 0; a < 5; ++a)
+        for (int c = 0; c < 5; ++c) {
+          const T tt = S0[0][a] * S0[2][c] + T(0.5) * DS[0][a] * S0[2][c] + T(0.5) * S0[0][a] * DS[2][c] +
+                       DS[0][a] * DS[2][c] * third;
+          T run = T(0);
+          for (int b = 0; b < 4; ++b) {
+            run += DS[1][b] * tt;
+            if (run != T(0)) atomicAdd(f.c[JY] + (size_t)jx[a] * g.nyz + (size_t)jy[b] * g.nz + jz[c], cf * run);
+          }
+        }
+    }
+    {  // Jz
+      const T cf = qw * jc[2];
+      for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) {
+          const T tt = S0[0][a] * S0[1][b] + T(0.5) * DS[0][a] * S0[1][b] + T(0.5) * S0[0][a] * DS[1][b] +
+                       DS[0][a] * DS[1][b] * third;
+          T run = T(0);
+          for (int c = 0; c < 4; ++c) {
+            run += DS[2][c] * tt;
+            if (run != T(0)) atomicAdd(f.c[JZ] + (size_t)jx[a] * g.nyz + (size_t)jy[b] * g.nz + jz[c], cf * run);
+          }
+        }
+    }
+
+    // store the advanced particle (cell wrapped into the ring / periodic box)
+    const int nx1 = wrapi(c0[0] + dc[0], g.nx);
+    const int ny1 = wrapi(c0[1] + dc[1], g.ny);
+    const int nz1 = wrapi(c0[2] + dc[2], g.nz);
+    p.cell[pi] = nx1 * g.nyz + ny1 * g.nz + nz1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      p.o[d][pi] = o1[d];
+      p.u[d][pi] = u[d];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Laser: boundary source on the window's back plane, and in-box start.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_hard_source(Geom<T> g, T* Ey, Laser L, double x_plane, double t, double dy, double dz) {
+  const int n = g.nyz;
+  const int s = slab_of(g, 0);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int j = r / g.nz, k = r - j * g.nz;
+    Ey[(size_t)s * n + r] = (T)laser_ey(L, x_plane, (j + 0.5) * dy, k * dz, t);
+  }
+}
+
+// In-box start, part 1: Ey(t) at its nodes and Bz(t + dt/2) at its nodes.
+template <typename T>
+__global__ void k_laser_fill(Geom<T> g, T* Ey, T* Bz, Laser L, double xnode0, double dx, double dy, double dz,
+                             double t, double dt) {
+  const long long ncell = (long long)g.nx * g.nyz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q / g.nyz);
+    const int r = (int)(q - (long long)i * g.nyz);
+    const int j = r / g.nz, k = r - j * g.nz;
+    const size_t id = (size_t)slab_of(g, i) * g.nyz + r;
+    Ey[id] = (T)laser_ey(L, xnode0 + i * dx, (j + 0.5) * dy, k * dz, t);
+    Bz[id] = (T)laser_ey(L, xnode0 + (i + 0.5) * dx, (j + 0.5) * dy, k * dz, t + 0.5 * dt);
+  }
+}
+
+// In-box start, part 2: Ex from the discrete Gauss law and Bx from the
+// discrete div B = 0, integrated from the back face (one thread per line).
+template <typename T>
+__global__ void k_laser_scan(Geom<T> g, const T* Ey, T* Ex, const T* Bz, T* Bx) {
+  const int n = g.nyz;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int j = r / g.nz, k = r - j * g.nz;
+    const int jm = j == 0 ? g.ny - 1 : j - 1, kp = k + 1 == g.nz ? 0 : k + 1;
+    T ex = T(0), bx = T(0);
+    for (int i = 0; i < g.nx; ++i) {
+      const size_t sb = (size_t)slab_of(g, i) * n;
+      ex -= g.dx * (Ey[sb + j * g.nz + k] - Ey[sb + jm * g.nz + k]) / g.dy;
+      Ex[sb + r] = ex;
+      Bx[sb + r] = bx;
+      bx -= g.dx * (Bz[sb + j * g.nz + kp] - Bz[sb + j * g.nz + k]) / g.dz;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_add(T* dst, const T* src, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    dst[q] += src[q];
+}
+
+// ---------------------------------------------------------------------------
+// Plasma loading / window injection (Sec. 3.1 profile, SplitMix64 keys).
+// One thread per (cell, slot) of relative x cells [lo, hi].
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T one_below();
+template <>
+__device__ __forceinline__ float one_below<float>() { return 0.99999994f; }
+template <>
+__device__ __forceinline__ double one_below<double>() { return 0.99999999999999989; }
+
+struct LoadSpec {
+  long long shifts;   // window shifts so far: lab cell = shifts + relative cell
+  int lo, hi;         // relative x cells to load
+  int ppc, lattice;
+  int ns[3];          // sub-lattice of the jittered lattice
+  uint64_t seed;
+  double x0, dx, dVppc;  // normalised; dV / ppc
+  const double* px;
+  const double* pn;
+  int np;
+  int capacity;
+};
+
+template <typename T>
+__global__ void k_load(Geom<T> g, Parts<T> p, int* d_np, int* d_err, LoadSpec L) {
+  const long long nslot = (long long)(L.hi - L.lo + 1) * g.nyz * L.ppc;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q0 = (long long)blockIdx.x * blockDim.x; q0 < nslot; q0 += stride) {
+    const long long q = q0 + threadIdx.x;
+    bool want = false;
+    double o[3] = {0, 0, 0}, n = 0;
+    int ci = 0, j = 0, k = 0, sl = 0;
+    unsigned long long cell = 0;
+    if (q < nslot) {
+      sl = (int)(q % L.ppc);
+      const long long c = q / L.ppc;
+      const int r = (int)(c % g.nyz);
+      ci = L.lo + (int)(c / g.nyz);
+      j = r / g.nz;
+      k = r - j * g.nz;
+      const long long lab = L.shifts + ci;
+      cell = ((unsigned long long)lab * g.ny + j) * g.nz + k;
+      const unsigned long long ctr = (cell * L.ppc + sl) * 3ull;
+      double rr[3];
+      for (int d = 0; d < 3; ++d) rr[d] = unit_uniform(L.seed, ctr + d);
+      if (L.lattice) {
+        const int sx = sl / (L.ns[1] * L.ns[2]), sy = (sl / L.ns[2]) % L.ns[1], sz = sl % L.ns[2];
+        o[0] = (sx + rr[0]) / L.ns[0];
+        o[1] = (sy + rr[1]) / L.ns[1];
+        o[2] = (sz + rr[2]) / L.ns[2];
+      } else {
+        o[0] = rr[0];
+        o[1] = rr[1];
+        o[2] = rr[2];
+      }
+      n = profile_at(L.px, L.pn, L.np, L.x0 + ((double)lab + o[0]) * L.dx);
+      want = n > 0.0;
+    }
+    const int slot = warp_append(d_np, want);
+    if (want) {
+      if (slot >= L.capacity) {
+        atomicOr(d_err, 1);
+      } else {
+        const int s = slab_of(g, ci);
+        p.cell[slot] = s * g.nyz + j * g.nz + k;
+        for (int d = 0; d < 3; ++d) {
+          T od = (T)o[d];
+          if (od >= T(1)) od = one_below<T>();  // rounding to float may reach 1
+          p.o[d][slot] = od;
+          p.u[d][slot] = T(0);
+        }
+        p.w[slot] = (T)(n * L.dVppc);
+        if (p.id) p.id[slot] = (uint32_t)(cell * L.ppc + sl);
+      }
+    }
+  }
+}
+
+// After loading or injection the counter may exceed the capacity (the
+// overflowing particles were not written and the error bit is set): clamp it.
+__global__ void k_clamp_count(int* d_np, int capacity) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && *d_np > capacity) *d_np = capacity;
+}
+
+// Drop particles outside the allowed relative x cells [lo, hi] (open x),
+// compacting into a second buffer with warp-aggregated appends.
+template <typename T>
+__global__ void k_compact(Geom<T> g, Parts<T> src, const int* __restrict__ d_np_src, Parts<T> dst,
+                          int* d_np_dst, int lo, int hi) {
+  const int n = *d_np_src;
+  const int stride = gridDim.x * blockDim.x;
+  for (int q0 = blockIdx.x * blockDim.x; q0 < n; q0 += stride) {
+    const int q = q0 + threadIdx.x;
+    bool keep = false;
+    int cell = 0;
+    if (q < n) {
+      cell = src.cell[q];
+      int rel = cell / g.nyz - g.origin;
+      if (rel < 0) rel += g.nx;
+      keep = rel >= lo && rel <= hi;
+    }
+    const int slot = warp_append(d_np_dst, keep);
+    if (keep) {
+      dst.cell[slot] = cell;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        dst.o[d][slot] = src.o[d][q];
+        dst.u[d][slot] = src.u[d][q];
+      }
+      dst.w[slot] = src.w[q];
+      if (dst.id) dst.id[slot] = src.id[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics (FP64 reductions).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? red[lane] : 0.0;
+  if (wid == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_field_energy(Geom<T> g, Fields<T> f, double* out) {
+  const long long n = (long long)g.nx * g.nyz;
+  double acc = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    for (int c = EX; c <= BZ; ++c) {
+      const double v = (double)f.c[c][q];
+      acc += v * v;
+    }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
+template <typename T>
+__global__ void k_lineout(Geom<T> g, const T* Ex, double* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x)
+    out[i] = (double)Ex[(size_t)slab_of(g, i) * g.nyz + (size_t)(g.ny / 2) * g.nz + g.nz / 2];
+}
+
+// kind 0: sum of w over gamma > gmin into out[0]; kind 1: histogram of
+// (gamma - 1) * mc2 over [e0, e1) into nb bins.
+template <typename T>
+__global__ void __launch_bounds__(256) k_particle_diag(Parts<T> p, const int* __restrict__ d_np, int kind,
+                                                      double gmin, double mc2, double e0, double e1, int nb,
+                                                      double* out) {
+  const int n = *d_np;
+  double acc = 0.0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const double ux = p.u[0][q], uy = p.u[1][q], uz = p.u[2][q];
+    const double gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+    const double w = (double)p.w[q];
+    if (kind == 0) {
+      if (gam > gmin) acc += w;
+    } else {
+      const double e = (gam - 1.0) * mc2;
+      if (e >= e0 && e < e1) {
+        int b = (int)floor((e - e0) / (e1 - e0) * nb);
+        if (b >= nb) b = nb - 1;
+        atomicAdd(out + b, w);
+      }
+    }
+  }
+  if (kind == 0) {
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) atomicAdd(out, acc);
+  }
+}
+
+}  // namespace pic

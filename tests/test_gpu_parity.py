@@ -1,0 +1,236 @@
+"""GPU (C-ABI) vs FP64 CPU oracle parity on seeded inputs.
+
+Tolerances: FP64 path <= 1e-10 relative per particle and per field value after
+one step; <= 1e-6 relative on integrated diagnostics after 100 steps (atomic
+accumulation order differs between runs at the 1e-16 level and particle
+orbits amplify it slowly).  Relative errors are normalised by max(|ref|max,
+RMS of ref) of the quantity compared.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1204_0838_gb300 import pic, workloads as W
+
+from .pairs import by_id, compare_fields, compare_particles, make_gpu, make_oracle, rel_err
+
+pytestmark = pytest.mark.gpu
+
+LAM = W.LAMBDA0
+C0 = W.C0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    pic.lib()
+
+
+def _pair(shape, periodic, dx=LAM / 8, dy=LAM / 3, dz=LAM / 2, precision="fp64"):
+    g = pic.Sim(*shape, dx, dy, dz, LAM, periodic_x=periodic, precision=precision, track_ids=True)
+    o = O.Sim(*shape, dx, dy, dz, LAM, periodic_x=periodic)
+    return g, o
+
+
+def _set_random(g, o, shape, npart, seed, periodic, umax=3.0):
+    inf = o.info()
+    dV = inf["dx"] * inf["dy"] * inf["dz"]
+    F, xi, u, w, ids = W.random_state(shape, npart, seed, umax=umax, periodic_x=periodic, dV=dV)
+    for s in (g, o):
+        s.set_fields(F)
+        if npart:
+            s.set_particles(xi, u, w, ids)
+
+
+# ---------------------------------------------------------------------------
+# field solver alone
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("periodic,shape", [(True, (32, 16, 16)), (False, (48, 16, 8)),
+                                            (True, (17, 5, 7))])
+def test_field_update_parity(periodic, shape):
+    g, o = _pair(shape, periodic)
+    _set_random(g, o, shape, 0, seed=1, periodic=periodic)
+    g.step(1)
+    o.step(1)
+    compare_fields(g, o, 1e-12)
+    g.step(9)
+    o.step(9)
+    compare_fields(g, o, 1e-11)
+
+
+def test_plane_wave_exact_shift_on_gpu():
+    shape = (128, 4, 4)
+    g, _ = _pair(shape, True, dy=LAM / 2, dz=LAM / 2)
+    dx = g.info()["dx"]
+    x = np.arange(shape[0]) * dx
+    ey = np.exp(-((x - x.mean()) / (6 * dx)) ** 2) * np.sin(2 * np.pi * x / (8 * dx))
+    bz = 0.5 * (ey + np.roll(ey, -1))
+    g.set_field(1, ey[:, None, None])
+    g.set_field(5, bz[:, None, None])
+    g.step(1000)
+    assert np.abs(g.field(1)[:, 2, 1] - np.roll(ey, 1000)).max() < 1e-12
+    assert np.abs(g.field(5)[:, 0, 3] - np.roll(bz, 1000)).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# one full step with random particles and fields
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("periodic,shape,npart", [(True, (32, 16, 16), 20000),
+                                                  (False, (48, 16, 8), 20000),
+                                                  (True, (16, 4, 4), 3000)])
+def test_one_step_parity_random_state(periodic, shape, npart):
+    g, o = _pair(shape, periodic)
+    _set_random(g, o, shape, npart, seed=2, periodic=periodic)
+    g.step(1)
+    o.step(1)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+
+
+def test_one_step_parity_c0_size():
+    cfg = W.config("c0")
+    shape = (cfg["nx"], cfg["ny"], cfg["nz"])
+    g, o = _pair(shape, False, cfg["dx"], cfg["dy"], cfg["dz"])
+    _set_random(g, o, shape, 126000, seed=3, periodic=False, umax=5.0)
+    g.step(1)
+    o.step(1)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+
+
+def test_absorbing_boundary_drops_same_particles():
+    shape = (32, 8, 8)
+    g, o = _pair(shape, False)
+    _set_random(g, o, shape, 5000, seed=4, periodic=False, umax=20.0)
+    for _ in range(4):
+        g.step(1)
+        o.step(1)
+        assert g.info()["np"] == o.info()["np"]
+    compare_particles(g.particles(), o.particles(), 1e-10)
+
+
+# ---------------------------------------------------------------------------
+# configured runs: loading, laser, window, diagnostics
+# ---------------------------------------------------------------------------
+def _diags(s, nx):
+    return {"energy": s.diag("field_energy")[0],
+            "lineout": s.diag("ex_lineout", nx),
+            "charge": s.diag("charge", 1, 0.0)[0],
+            "charge_hot": s.diag("charge", 1, 1.0001)[0],
+            "spectrum": s.diag("spectrum", 64, 0.0, 0.2)}
+
+
+def _compare_diags(dg, do, tol):
+    assert abs(dg["energy"] / do["energy"] - 1) <= tol
+    assert np.linalg.norm(dg["lineout"] - do["lineout"]) <= tol * np.linalg.norm(do["lineout"])
+    assert abs(dg["charge"] / do["charge"] - 1) <= tol
+    if do["charge_hot"] > 0:
+        assert abs(dg["charge_hot"] / do["charge_hot"] - 1) <= tol
+    assert np.abs(dg["spectrum"] - do["spectrum"]).sum() <= tol * do["spectrum"].sum() + 1e-300
+
+
+def test_c0_loading_matches_oracle():
+    cfg = W.config("c0")
+    g, o = make_gpu(cfg), make_oracle(cfg)
+    compare_particles(g.particles(), o.particles(), 1e-15)
+    compare_fields(g, o, 1e-15)
+
+
+@pytest.mark.slow
+def test_c0_100_steps_diagnostics():
+    cfg = W.config("c0")
+    g, o = make_gpu(cfg), make_oracle(cfg)
+    g.step(1)
+    o.step(1)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+    g.step(99)
+    o.step(99)
+    _compare_diags(_diags(g, cfg["nx"]), _diags(o, cfg["nx"]), 1e-6)
+
+
+def _window_cfg():
+    """Cropped c1: same spacings, window at c, plasma edge inside the box, a
+    short pulse so that it fits the cropped box."""
+    cfg = W.config("c1", crop=(96, 24, 24))
+    cfg["x0"] = -48 * cfg["dx"]
+    cfg["fwhm"] = 4e-15
+    cfg["waist"] = 3e-6
+    cfg["t_peak"] = 40 * cfg["dx"] / C0  # envelope centre 40 cells behind the focus at t = 0
+    cfg["prof_x"] = [0.0, 2e-6, 1.0]
+    cfg["prof_n"] = [0.0, 0.02, 0.02]
+    return cfg
+
+
+def test_window_run_diagnostics_and_injection():
+    cfg = _window_cfg()
+    g, o = make_gpu(cfg), make_oracle(cfg)
+    compare_particles(g.particles(), o.particles(), 1e-15)
+    compare_fields(g, o, 1e-12)
+    g.step(1)
+    o.step(1)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+    g.step(59)
+    o.step(59)
+    ig, io = g.info(), o.info()
+    assert ig["shifts"] == io["shifts"] == 60
+    assert ig["np"] == io["np"]
+    _compare_diags(_diags(g, cfg["nx"]), _diags(o, cfg["nx"]), 1e-6)
+    compare_particles(g.particles(), o.particles(), 1e-6)
+
+
+def test_fp32_against_fp64_diagnostics():
+    cfg = _window_cfg()
+    g64 = make_gpu(cfg, precision="fp64")
+    g32 = make_gpu(cfg, precision="fp32")
+    g64.step(60)
+    g32.step(60)
+    d64, d32 = _diags(g64, cfg["nx"]), _diags(g32, cfg["nx"])
+    assert np.linalg.norm(d32["lineout"] - d64["lineout"]) <= 0.01 * np.linalg.norm(d64["lineout"])
+    assert abs(d32["energy"] / d64["energy"] - 1) <= 0.01
+    assert abs(d32["charge"] / d64["charge"] - 1) <= 0.02
+
+
+def test_batched_equals_single_fp32():
+    cfg = _window_cfg()
+    singles = [make_gpu(dict(cfg, seed=cfg["seed"] + i, a0=2 + i), precision="fp32") for i in range(3)]
+    batch_members = [make_gpu(dict(cfg, seed=cfg["seed"] + i, a0=2 + i), precision="fp32") for i in range(3)]
+    b = pic.pic_batch_create([m.h for m in batch_members])
+    try:
+        pic.pic_batch_step(b, 20)
+        for s in singles:
+            s.step(20)
+        for i, s in enumerate(singles):
+            e_b = pic.pic_batch_diag(b, i, pic.PIC_DIAG_FIELD_ENERGY)[0]
+            assert abs(e_b / s.diag("field_energy")[0] - 1) < 1e-4
+            lb = pic.pic_batch_diag(b, i, pic.PIC_DIAG_EX_LINEOUT, cfg["nx"])
+            ls = s.diag("ex_lineout", cfg["nx"])
+            assert np.linalg.norm(lb - ls) <= 1e-4 * np.linalg.norm(ls)
+        with pytest.raises(pic.PicError):
+            batch_members[0].step(1)  # members are stepped by their batch only
+    finally:
+        pic.pic_batch_destroy(b)
+
+
+# ---------------------------------------------------------------------------
+# error behaviour of the C-ABI (host-side checks; nothing faults the GPU)
+# ---------------------------------------------------------------------------
+def test_error_codes():
+    with pytest.raises(pic.PicError) as e:
+        pic.Sim(32, 8, 8, LAM / 2, LAM / 4, LAM / 2, LAM)  # dx > dy violates Sec. 2
+    assert e.value.code == -1
+    with pytest.raises(pic.PicError):
+        pic.Sim(32, 8, 8, LAM / 8, LAM / 4, LAM / 2, LAM, dt=1.1 * LAM / 8 / C0)
+    g = pic.Sim(32, 8, 8, LAM / 8, LAM / 4, LAM / 2, LAM, periodic_x=False, max_particles=100)
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_add_species(g.h, [-1, 1], [0.01, 0.01], 1, spline_order=2)
+    assert e.value.code == -1
+    with pytest.raises(pic.PicError) as e:
+        g.add_species([-1, 1], [0.01, 0.01], 1)  # 27 cells x 64 > 100 particles
+    assert e.value.code == -4
+    with pytest.raises(pic.PicError) as e:
+        g.set_particles(np.array([[0.5], [1.0], [1.0]]), np.zeros((3, 1)), np.ones(1))
+    assert e.value.code == -1  # x cell 0 is outside the open-x allowed range
