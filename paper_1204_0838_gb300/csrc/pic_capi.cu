@@ -7,13 +7,14 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "../../include/pic.h"
-#include "pic_kernels.cuh"
+#include "pic_tiled.cuh"
 #include "pic_runtime.h"
 
 using namespace pic;
@@ -201,6 +202,8 @@ int ensure_particles(pic_t* h, long long cap) {
     nb[b].w = take(es * cap);
     nb[b].id = ids ? (uint32_t*)take(4 * (size_t)cap) : nullptr;
   }
+  int* nkeys = (int*)dalloc(h, 4 * (size_t)cap);
+  if (!nkeys) return fail(h, PIC_ERR_OOM, "particle key allocation failed");
   // carry the live particles over
   int np = 0;
   if (h->capacity > 0) {
@@ -219,11 +222,14 @@ int ensure_particles(pic_t* h, long long cap) {
     CK(h, cudaStreamSynchronize(h->stream));
     dfree(h, h->pb[0].base);
     dfree(h, h->pb[1].base);
+    dfree(h, h->keys);
   }
   h->pb[0] = nb[0];
   h->pb[1] = nb[1];
+  h->keys = nkeys;
   h->cur = 0;
   h->capacity = cap;
+  h->need_sort = true;
   CK(h, cudaMemcpyAsync(h->d_ctrl, &np, sizeof(int), cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   return PIC_OK;
@@ -327,73 +333,264 @@ int laser_in_box(pic_t* h) {
 }
 
 template <typename T>
-int shift_window(pic_t* h) {
-  // the back slab leaves; its storage becomes the new, empty front slab
-  const int front_storage = h->origin;
-  h->origin = (h->origin + 1) % h->nx;
-  h->shifts += 1;
+FieldCoef<T> field_coef(const pic_t* h) {
+  FieldCoef<T> c;
+  c.dt = (T)h->dt;
+  c.hdt = (T)(0.5 * h->dt);
+  c.idx = (T)(1.0 / h->dx);
+  c.idy = (T)(1.0 / h->dy);
+  c.idz = (T)(1.0 / h->dz);
+  return c;
+}
+
+template <typename T>
+Fields<T> curl_view(const pic_t* h) {
+  Fields<T> c;
+  for (int i = 0; i < NCOMP; ++i) c.c[i] = nullptr;
+  for (int i = 0; i < 3; ++i) c.c[i] = (T*)h->curl + (size_t)i * h->ncell;
+  return c;
+}
+
+// C = curl'(E) over window-relative slabs [i0, i0 + ni).
+template <typename T>
+int curl_only(pic_t* h, int i0, int ni) {
+  GroupTimer tm(h, G_FIELD);
+  counted(h, G_FIELD);
+  k_curl_update<T><<<grid_for((long long)ni * h->ny * h->nz), 256, 0, h->stream>>>(
+      geom<T>(h), smooth<T>(h), fields<T>(h), curl_view<T>(h), field_coef<T>(h), 0, i0, ni);
+  CK(h, cudaGetLastError());
+  return PIC_OK;
+}
+
+// Counting sort of the current buffer by tile into the other buffer.
+template <typename T>
+int resort_all(pic_t* h) {
+  if (!h->tiled || h->capacity == 0) return PIC_OK;
+  const int nb = 1 - h->cur;
+  const Tiles tl = h->tiles;
+  GroupTimer tm(h, G_PART);
+  CK(h, cudaMemsetAsync(h->tcnt, 0, sizeof(int) * tl.n, h->stream));
+  CK(h, cudaMemsetAsync(h->tfill, 0, sizeof(int) * tl.n, h->stream));
+  k_keys<T><<<grid_for(h->capacity, 256, 152 * 16), 256, 0, h->stream>>>(geom<T>(h), tl, parts<T>(h, h->cur),
+                                                                         h->d_ctrl + h->cur, h->keys, h->tcnt);
+  k_scan_tiles<<<1, 1024, 0, h->stream>>>(h->tcnt, h->tstart[nb], tl.n, h->d_ctrl + nb, (int)h->capacity,
+                                          h->d_ctrl + 2);
+  k_scatter<T><<<grid_for(h->capacity, 256, 152 * 16), 256, 0, h->stream>>>(
+      parts<T>(h, h->cur), h->keys, h->d_ctrl + h->cur, parts<T>(h, nb), h->tstart[nb], h->tfill, h->d_ctrl + 2);
+  counted(h, G_PART, 3);
+  CK(h, cudaGetLastError());
+  h->cur = nb;
+  return PIC_OK;
+}
+
+LoadSpec load_spec(const pic_t* h, int lo, int hi) {
+  LoadSpec L;
+  L.shifts = h->shifts;
+  L.lo = lo;
+  L.hi = hi;
+  L.ppc = h->ppc;
+  L.lattice = h->loading == PIC_LOAD_LATTICE;
+  for (int d = 0; d < 3; ++d) L.ns[d] = h->lat[d];
+  L.seed = h->seed;
+  L.x0 = h->x0;
+  L.dx = h->dx;
+  L.dVppc = h->dx * h->dy * h->dz / h->ppc;
+  L.px = h->d_prof;
+  L.pn = h->d_prof + h->nprof;
+  L.np = h->nprof;
+  L.capacity = (int)h->capacity;
+  return L;
+}
+
+// Window decision for the step that ends at t_new: returns 1 if the window
+// moves one cell at the end of this step (v <= c and c dt <= dx: at most one).
+int window_due(pic_t* h, double t_old, double t_new, double* frac_new) {
+  *frac_new = h->win_frac;
+  if (!h->has_window || !(t_new > h->win_t0)) return 0;
+  *frac_new = h->win_frac + h->win_v * (t_old >= h->win_t0 ? h->dt : (t_new - h->win_t0)) / h->dx;
+  return *frac_new >= 1.0 ? 1 : 0;
+}
+
+template <typename T>
+int zero_front_slab(pic_t* h, int storage_slab) {
   Fields<T> f = fields<T>(h);
   const size_t slab = (size_t)h->ny * h->nz;
   for (int c = 0; c < NCOMP; ++c)
-    CK(h, cudaMemsetAsync(f.c[c] + (size_t)front_storage * slab, 0, slab * sizeof(T), h->stream));
-  int rc = compact<T>(h);
+    CK(h, cudaMemsetAsync(f.c[c] + (size_t)storage_slab * slab, 0, slab * sizeof(T), h->stream));
+  return PIC_OK;
+}
+
+template <typename T>
+int field_first_half(pic_t* h) {
+  if (!h->curl_valid) {
+    int rc = curl_only<T>(h, 0, h->nx);
+    if (rc) return rc;
+    h->curl_valid = true;
+  }
+  GroupTimer tm(h, G_FIELD);
+  counted(h, G_FIELD);
+  k_e_update<T><<<grid_for(h->ncell), 256, 0, h->stream>>>(geom<T>(h), fields<T>(h), curl_view<T>(h),
+                                                           field_coef<T>(h));
+  CK(h, cudaGetLastError());
+  return PIC_OK;
+}
+
+template <typename T>
+int field_second_half(pic_t* h) {
+  GroupTimer tm(h, G_FIELD);
+  counted(h, G_FIELD);
+  k_curl_update<T><<<grid_for(h->ncell), 256, 0, h->stream>>>(geom<T>(h), smooth<T>(h), fields<T>(h),
+                                                              curl_view<T>(h), field_coef<T>(h), 1, 0, h->nx);
+  CK(h, cudaGetLastError());
+  return PIC_OK;
+}
+
+// After a shift the storage slab that left at the back is the new, zeroed
+// front slab; the cached curl is recomputed where the window edges moved.
+template <typename T>
+int after_shift_fields(pic_t* h, int old_origin) {
+  int rc = zero_front_slab<T>(h, old_origin);
   if (rc) return rc;
-  if (h->has_species) return load_cells<T>(h, x_hi(h), x_hi(h));
+  if (h->curl_valid) {
+    rc = curl_only<T>(h, 0, 1);
+    if (!rc) rc = curl_only<T>(h, h->nx - 1, 1);
+  }
+  return rc;
+}
+
+// One step with tile-sorted particles.
+template <typename T>
+int step_tiled(pic_t* h) {
+  const size_t n = h->ncell;
+  Fields<T> f = fields<T>(h);
+  const double t_old = (double)h->step * h->dt, t_new = (double)(h->step + 1) * h->dt;
+  double frac_new;
+  const int shift = window_due(h, t_old, t_new, &frac_new);
+  const int origin_after = shift ? (h->origin + 1) % h->nx : h->origin;
+  const Tiles tl = h->tiles;
+  const int nb = 1 - h->cur;
+  CK(h, cudaMemsetAsync(f.c[JX], 0, 3 * n * sizeof(T), h->stream));
+  if (h->capacity > 0) {
+    CK(h, cudaMemsetAsync(h->tcnt, 0, sizeof(int) * tl.n, h->stream));
+    GroupTimer tm(h, G_PUSH);
+    counted(h, G_PUSH);
+    const T hq = (T)(h->q * h->dt / (2.0 * h->m));
+    k_push_tiled<T><<<tl.n, 256, tiled_smem_bytes<T>(tl), h->stream>>>(
+        geom<T>(h), tl, f, parts<T>(h, h->cur), h->tstart[h->cur], (int)h->capacity, h->keys, h->tcnt, hq,
+        (T)h->q, origin_after, x_lo(h), x_hi(h), h->d_pushed, h->d_ctrl + 2);
+    CK(h, cudaGetLastError());
+  }
+  int rc = field_first_half<T>(h);
+  if (rc) return rc;
+  h->step += 1;
+  if (h->laser_mode == PIC_LASER_HARD_SOURCE) {
+    rc = hard_source<T>(h, t_new);
+    if (rc) return rc;
+  }
+  rc = field_second_half<T>(h);
+  if (rc) return rc;
+  h->win_frac = frac_new;
+  LoadSpec L;
+  if (shift) {
+    h->win_frac -= 1.0;
+    const int old_origin = h->origin;
+    h->origin = origin_after;
+    h->shifts += 1;
+    rc = after_shift_fields<T>(h, old_origin);
+    if (rc) return rc;
+  }
+  if (h->capacity == 0) return PIC_OK;
+  GroupTimer tm(h, G_PART);
+  const bool inject = shift && h->has_species;
+  if (inject) {
+    L = load_spec(h, x_hi(h), x_hi(h));
+    const long long nslot = (long long)h->ny * h->nz * h->ppc;
+    k_inject_tiled<T><<<grid_for(nslot, 256, 152 * 16), 256, 0, h->stream>>>(
+        geom<T>(h), tl, parts<T>(h, nb), L, 0, h->tcnt, h->tstart[nb], h->tfill, h->d_ctrl + 2);
+    counted(h, G_PART);
+  }
+  k_scan_tiles<<<1, 1024, 0, h->stream>>>(h->tcnt, h->tstart[nb], tl.n, h->d_ctrl + nb, (int)h->capacity,
+                                          h->d_ctrl + 2);
+  CK(h, cudaMemsetAsync(h->tfill, 0, sizeof(int) * tl.n, h->stream));
+  k_scatter<T><<<grid_for(h->capacity, 256, 152 * 16), 256, 0, h->stream>>>(
+      parts<T>(h, h->cur), h->keys, h->d_ctrl + h->cur, parts<T>(h, nb), h->tstart[nb], h->tfill, h->d_ctrl + 2);
+  counted(h, G_PART, 2);
+  if (inject) {
+    const long long nslot = (long long)h->ny * h->nz * h->ppc;
+    k_inject_tiled<T><<<grid_for(nslot, 256, 152 * 16), 256, 0, h->stream>>>(
+        geom<T>(h), tl, parts<T>(h, nb), L, 1, h->tcnt, h->tstart[nb], h->tfill, h->d_ctrl + 2);
+    counted(h, G_PART);
+  }
+  CK(h, cudaGetLastError());
+  h->cur = nb;
+  return PIC_OK;
+}
+
+// One step with the unsorted one-thread-per-particle kernel and stream
+// compaction (kept for comparison; selected with PIC_KERNEL=simple).
+template <typename T>
+int step_simple(pic_t* h) {
+  const size_t n = h->ncell;
+  Fields<T> f = fields<T>(h);
+  const double t_old = (double)h->step * h->dt, t_new = (double)(h->step + 1) * h->dt;
+  double frac_new;
+  const int shift = window_due(h, t_old, t_new, &frac_new);
+  CK(h, cudaMemsetAsync(f.c[JX], 0, 3 * n * sizeof(T), h->stream));
+  if (h->capacity > 0) {
+    GroupTimer tm(h, G_PUSH);
+    counted(h, G_PUSH);
+    const T hq = (T)(h->q * h->dt / (2.0 * h->m));
+    k_push_deposit<T><<<grid_for(h->capacity, 256, 152 * 16), 256, 0, h->stream>>>(
+        geom<T>(h), f, parts<T>(h, h->cur), h->d_ctrl + h->cur, hq, (T)h->q, h->d_pushed);
+  }
+  int rc = field_first_half<T>(h);
+  if (rc) return rc;
+  h->step += 1;
+  if (h->laser_mode == PIC_LASER_HARD_SOURCE) {
+    rc = hard_source<T>(h, t_new);
+    if (rc) return rc;
+  }
+  rc = field_second_half<T>(h);
+  if (rc) return rc;
+  h->win_frac = frac_new;
+  if (shift) {
+    h->win_frac -= 1.0;
+    const int old_origin = h->origin;
+    h->origin = (h->origin + 1) % h->nx;
+    h->shifts += 1;
+    rc = after_shift_fields<T>(h, old_origin);
+    if (rc) return rc;
+  }
+  if (h->capacity > 0 && !h->periodic_x) {
+    rc = compact<T>(h);
+    if (rc) return rc;
+  }
+  if (shift && h->has_species) return load_cells<T>(h, x_hi(h), x_hi(h));
   return PIC_OK;
 }
 
 template <typename T>
 int step_impl(pic_t* h, int nsteps) {
-  const size_t n = h->ncell;
+  if (h->need_sort && nsteps > 0) {
+    int rc = resort_all<T>(h);
+    if (rc) return rc;
+    h->need_sort = false;
+  }
   for (int it = 0; it < nsteps; ++it) {
-    Fields<T> f = fields<T>(h);
-    const double t_old = (double)h->step * h->dt;
-    CK(h, cudaMemsetAsync(f.c[JX], 0, 3 * n * sizeof(T), h->stream));
-    if (h->capacity > 0) {
-      GroupTimer tm(h, G_PUSH);
-      counted(h, G_PUSH);
-      const T hq = (T)(h->q * h->dt / (2.0 * h->m));
-      k_push_deposit<T><<<grid_for(h->capacity, 256, 152 * 16), 256, 0, h->stream>>>(
-          geom<T>(h), f, parts<T>(h, h->cur), h->d_ctrl + h->cur, hq, (T)h->q, h->d_pushed);
-    }
-    const Geom<T> g = geom<T>(h);
-    const Smooth<T> S = smooth<T>(h);
-    {
-      GroupTimer tm(h, G_FIELD);
-      counted(h, G_FIELD, 2);
-      k_curl_e<T><<<grid_for(n), 256, 0, h->stream>>>(g, S, f.c[EX], f.c[EY], f.c[EZ], f.c[BX], f.c[BY],
-                                                       f.c[BZ], (T)(-0.5 * h->dt));
-      k_curl_b<T><<<grid_for(n), 256, 0, h->stream>>>(g, f);
-    }
-    h->step += 1;
-    const double t_new = (double)h->step * h->dt;
-    if (h->laser_mode == PIC_LASER_HARD_SOURCE) {
-      int rc = hard_source<T>(h, t_new);
-      if (rc) return rc;
-    }
-    {
-      GroupTimer tm(h, G_FIELD);
-      counted(h, G_FIELD);
-      k_curl_e<T><<<grid_for(n), 256, 0, h->stream>>>(g, S, f.c[EX], f.c[EY], f.c[EZ], f.c[BX], f.c[BY],
-                                                       f.c[BZ], (T)(-0.5 * h->dt));
-    }
-    CK(h, cudaGetLastError());
-    bool compacted = false;
-    if (h->has_window && t_new > h->win_t0) {
-      h->win_frac += h->win_v * (t_old >= h->win_t0 ? h->dt : (t_new - h->win_t0)) / h->dx;
-      while (h->win_frac >= 1.0) {
-        h->win_frac -= 1.0;
-        int rc = shift_window<T>(h);
-        if (rc) return rc;
-        compacted = true;
-      }
-    }
-    if (!h->periodic_x && h->capacity > 0 && !compacted) {
-      int rc = compact<T>(h);
-      if (rc) return rc;
-    }
+    int rc = h->tiled ? step_tiled<T>(h) : step_simple<T>(h);
+    if (rc) return rc;
   }
   return PIC_OK;
+}
+
+int check_device_error(pic_t* h);
+
+// Between calls: if the live count is within 20% of the capacity and the
+// caller did not fix the capacity, grow the buffers by half.
+int grow_if_needed(pic_t* h) {
+  if (h->capacity == 0 || h->max_particles > 0) return PIC_OK;
+  if ((double)h->np_host < 0.8 * (double)h->capacity) return PIC_OK;
+  return ensure_particles(h, std::min<long long>(0x7fffffffLL, h->capacity * 3 / 2 + 4096));
 }
 
 int check_device_error(pic_t* h) {
@@ -407,6 +604,7 @@ int check_device_error(pic_t* h) {
   if (ctrl[2] & 1) {
     return fail(h, PIC_ERR_CAPACITY, "particle capacity exceeded during loading/injection");
   }
+  if (ctrl[2] & 6) return fail(h, PIC_ERR_STATE, "tile bookkeeping error in the particle binning");
   return PIC_OK;
 }
 
@@ -525,9 +723,38 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
     h->has_alloc = true;
   }
   if (w) {
+    if (!(w->v >= 0.0 && w->v <= 1.0)) {
+      delete h;
+      return PIC_ERR_ARG;  // the window moves at most at c (one cell per step)
+    }
     h->has_window = true;
     h->win_v = w->v;
     h->win_t0 = w->t_start * h->omega0;
+  }
+  {
+    const char* kern = std::getenv("PIC_KERNEL");
+    h->tiled = !(kern && std::strcmp(kern, "simple") == 0);
+    int t3[3] = {8, 8, 8};
+    const char* ts = std::getenv("PIC_TILE");
+    if (ts) std::sscanf(ts, "%d,%d,%d", &t3[0], &t3[1], &t3[2]);
+    const int n3[3] = {h->nx, h->ny, h->nz};
+    for (int d = 0; d < 3; ++d) t3[d] = std::max(1, std::min(t3[d], n3[d]));
+    Tiles& tl = h->tiles;
+    tl.tx = t3[0];
+    tl.ty = t3[1];
+    tl.tz = t3[2];
+    // keep the shared-memory tile within the 227 KB a CTA may use
+    const size_t es = h->precision == PIC_FP64 ? 8 : 4;
+    while (es * (6 * (size_t)(tl.tx + 4) * (tl.ty + 4) * (tl.tz + 4) + 3 * (size_t)(tl.tx + 5) * (tl.ty + 5) * (tl.tz + 5)) >
+           227 * 1024) {
+      if (tl.tx >= tl.ty && tl.tx >= tl.tz) tl.tx /= 2;
+      else if (tl.ty >= tl.tz) tl.ty /= 2;
+      else tl.tz /= 2;
+    }
+    tl.ntx = (h->nx + tl.tx - 1) / tl.tx;
+    tl.nty = (h->ny + tl.ty - 1) / tl.ty;
+    tl.ntz = (h->nz + tl.tz - 1) / tl.tz;
+    tl.n = tl.ntx * tl.nty * tl.ntz;
   }
   set_coefficients(h);
   if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -537,6 +764,26 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
   }
   h->stream = h->own_stream;
   h->fields = dalloc(h, NCOMP * h->ncell * esize(h));
+  h->curl = dalloc(h, 3 * h->ncell * esize(h));
+  h->tstart[0] = (int*)dalloc(h, sizeof(int) * (h->tiles.n + 1));
+  h->tstart[1] = (int*)dalloc(h, sizeof(int) * (h->tiles.n + 1));
+  h->tcnt = (int*)dalloc(h, sizeof(int) * h->tiles.n);
+  h->tfill = (int*)dalloc(h, sizeof(int) * h->tiles.n);
+  if (!h->curl || !h->tstart[0] || !h->tstart[1] || !h->tcnt || !h->tfill) {
+    pic_destroy(h);
+    return PIC_ERR_OOM;
+  }
+  {
+    const size_t sm = h->precision == PIC_FP64 ? tiled_smem_bytes<double>(h->tiles) : tiled_smem_bytes<float>(h->tiles);
+    cudaError_t e = h->precision == PIC_FP64
+                        ? cudaFuncSetAttribute(k_push_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                        : cudaFuncSetAttribute(k_push_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      pic_destroy(h);
+      return PIC_ERR_CUDA;
+    }
+  }
   h->d_ctrl = (int*)dalloc(h, 64);
   h->d_pushed = h->d_ctrl ? (unsigned long long*)(h->d_ctrl + 4) : nullptr;
   if (!h->fields || !h->d_ctrl) {
@@ -544,6 +791,8 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
     return PIC_ERR_OOM;
   }
   if (cudaMemsetAsync(h->fields, 0, NCOMP * h->ncell * esize(h), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->tstart[0], 0, sizeof(int) * (h->tiles.n + 1), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->tstart[1], 0, sizeof(int) * (h->tiles.n + 1), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_ctrl, 0, 64, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -597,12 +846,14 @@ int pic_add_species(pic_t* h, const pic_profile* n, int ppc, int spline_order, d
   for (int d = 0; d < 3; ++d) h->lat[d] = lat[d];
   h->q = q;
   h->m = m;
-  long long cap = h->max_particles > 0 ? h->max_particles : (long long)h->ncell * ppc;
+  // default capacity: 25% above one full load, for compression by the wake
+  long long cap = h->max_particles > 0 ? h->max_particles : (long long)h->ncell * ppc * 5 / 4 + 4096;
   int rc = ensure_particles(h, cap);
   if (rc) return rc;
   h->has_species = true;
   rc = h->precision == PIC_FP64 ? load_cells<double>(h, x_lo(h), x_hi(h)) : load_cells<float>(h, x_lo(h), x_hi(h));
   if (rc) return rc;
+  h->need_sort = true;
   return check_device_error(h);
 }
 
@@ -626,6 +877,7 @@ int pic_add_laser(pic_t* h, double a0, double waist, double duration_fwhm, doubl
   h->laser_mode = mode;
   int rc;
   const double t = (double)h->step * h->dt;
+  h->curl_valid = false;
   if (mode == PIC_LASER_HARD_SOURCE)
     rc = h->precision == PIC_FP64 ? hard_source<double>(h, t) : hard_source<float>(h, t);
   else
@@ -638,7 +890,9 @@ int pic_add_laser(pic_t* h, double a0, double waist, double duration_fwhm, doubl
 int pic_step(pic_t* h, int n) {
   if (!h || n < 0) return PIC_ERR_ARG;
   if (h->batched) return fail(h, PIC_ERR_STATE, "handle is part of a batch");
-  int rc = h->precision == PIC_FP64 ? step_impl<double>(h, n) : step_impl<float>(h, n);
+  int rc = grow_if_needed(h);
+  if (rc) return rc;
+  rc = h->precision == PIC_FP64 ? step_impl<double>(h, n) : step_impl<float>(h, n);
   if (rc) return rc;
   return check_device_error(h);
 }
@@ -699,6 +953,7 @@ int pic_set_field(pic_t* h, int comp, const double* host_in) {
   CK(h, cudaMemcpyAsync((char*)h->fields + comp * h->ncell * es, buf.data(), h->ncell * es, cudaMemcpyHostToDevice,
                         h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  if (comp <= EZ) h->curl_valid = false;
   return PIC_OK;
 }
 
@@ -827,6 +1082,7 @@ int pic_set_particles(pic_t* h, const pic_particles* p) {
   CK(h, cudaMemcpyAsync(h->d_ctrl + h->cur, &npi, sizeof(int), cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   h->np_host = npi;
+  h->need_sort = true;
   return PIC_OK;
 }
 

@@ -29,6 +29,14 @@ struct Smooth {
   T a[3], b1[3], b2[3], g[3];
 };
 
+// Tiling of the storage-frame grid (x slabs in ring order) used to keep the
+// particles grouped; tiles at the high end of an axis may be ragged.
+struct Tiles {
+  int tx, ty, tz;     // tile extent in cells
+  int ntx, nty, ntz;  // tiles per axis
+  int n;              // ntx * nty * ntz
+};
+
 template <typename T>
 struct Fields {
   T* c[NCOMP];

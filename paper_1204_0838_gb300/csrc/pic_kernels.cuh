@@ -118,6 +118,98 @@ __global__ void __launch_bounds__(256) k_curl_b(Geom<T> g, Fields<T> f) {
 }
 
 // ---------------------------------------------------------------------------
+// Field update with a cached smoothed curl.  The two magnetic half steps of
+// consecutive steps use the same curl'(E^{n+1}), so it is computed once per
+// step and kept in C:
+//   k_e_update:     B^{n+1/2} = B^n - (dt/2) C^n (formed on the fly),
+//                   E^{n+1} = E^n + dt (curl B^{n+1/2} - J)
+//   k_curl_update:  C^{n+1} = curl'(E^{n+1}),
+//                   B^{n+1} = (B^n - (dt/2) C^n) - (dt/2) C^{n+1}
+// Reciprocal spacings are precomputed (no divisions in the loops).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct FieldCoef {
+  T dt, hdt;             // dt, dt/2
+  T idx, idy, idz;       // 1/dx, 1/dy, 1/dz
+};
+
+template <typename T>
+__device__ __forceinline__ T bhalf(const T* __restrict__ B, const T* __restrict__ C, const Geom<T>& g, int s,
+                                   int j, int k, T hdt) {
+  if (s < 0) return T(0);
+  j = (j < 0) ? j + g.ny : j;
+  k = (k < 0) ? k + g.nz : k;
+  const size_t id = (size_t)s * g.nyz + (size_t)j * g.nz + k;
+  return B[id] - hdt * C[id];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_e_update(Geom<T> g, Fields<T> f, Fields<T> cc, FieldCoef<T> fc) {
+  const int nyz = g.nyz;
+  const long long ncell = (long long)g.nx * nyz;
+  const T *Bx = f.c[BX], *By = f.c[BY], *Bz = f.c[BZ];
+  const T *Cx = cc.c[0], *Cy = cc.c[1], *Cz = cc.c[2];
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q / nyz);
+    const int r = (int)(q - (long long)i * nyz);
+    const int j = r / g.nz, k = r - j * g.nz;
+    const int s = slab_of(g, i), sm = slab_of(g, i - 1);
+    const size_t id = (size_t)s * nyz + r;
+    const T bx = Bx[id] - fc.hdt * Cx[id];
+    const T by = By[id] - fc.hdt * Cy[id];
+    const T bz = Bz[id] - fc.hdt * Cz[id];
+    const T cx = (bz - bhalf(Bz, Cz, g, s, j - 1, k, fc.hdt)) * fc.idy - (by - bhalf(By, Cy, g, s, j, k - 1, fc.hdt)) * fc.idz;
+    const T cy = (bx - bhalf(Bx, Cx, g, s, j, k - 1, fc.hdt)) * fc.idz - (bz - bhalf(Bz, Cz, g, sm, j, k, fc.hdt)) * fc.idx;
+    const T cz = (by - bhalf(By, Cy, g, sm, j, k, fc.hdt)) * fc.idx - (bx - bhalf(Bx, Cx, g, s, j - 1, k, fc.hdt)) * fc.idy;
+    f.c[EX][id] += fc.dt * (cx - f.c[JX][id]);
+    f.c[EY][id] += fc.dt * (cy - f.c[JY][id]);
+    f.c[EZ][id] += fc.dt * (cz - f.c[JZ][id]);
+  }
+}
+
+// Smoothed curl of E at one cell (Sec. 2: D_i replaced by D_i S_i).
+template <typename T>
+__device__ __forceinline__ void curl_smoothed(const Geom<T>& g, const Smooth<T>& S, const FieldCoef<T>& fc,
+                                              const T* Ex, const T* Ey, const T* Ez, int sm, int s, int sp, int j,
+                                              int k, T& cx, T& cy, T& cz) {
+  cx = (smooth_y(Ez, g, S, sm, s, sp, j + 1, k) - smooth_y(Ez, g, S, sm, s, sp, j, k)) * fc.idy -
+       (smooth_z(Ey, g, S, sm, s, sp, j, k + 1) - smooth_z(Ey, g, S, sm, s, sp, j, k)) * fc.idz;
+  cy = (smooth_z(Ex, g, S, sm, s, sp, j, k + 1) - smooth_z(Ex, g, S, sm, s, sp, j, k)) * fc.idz -
+       (smooth_x(Ez, g, S, sp, j, k) - smooth_x(Ez, g, S, s, j, k)) * fc.idx;
+  cz = (smooth_x(Ey, g, S, sp, j, k) - smooth_x(Ey, g, S, s, j, k)) * fc.idx -
+       (smooth_y(Ex, g, S, sm, s, sp, j + 1, k) - smooth_y(Ex, g, S, sm, s, sp, j, k)) * fc.idy;
+}
+
+// mode 0: C = curl'(E) only (start, or after E changed outside a step), over
+//         window-relative slabs [i0, i0 + ni);
+// mode 1: C^{n+1} = curl'(E^{n+1}) and the two B half steps, whole grid.
+template <typename T>
+__global__ void __launch_bounds__(256) k_curl_update(Geom<T> g, Smooth<T> S, Fields<T> f, Fields<T> cc,
+                                                    FieldCoef<T> fc, int mode, int i0, int ni) {
+  const int nyz = g.nyz;
+  const long long ncell = (long long)ni * nyz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = i0 + (int)(q / nyz);
+    const int r = (int)(q - (long long)(i - i0) * nyz);
+    const int j = r / g.nz, k = r - j * g.nz;
+    const int s = slab_of(g, i), sm = slab_of(g, i - 1), sp = slab_of(g, i + 1);
+    T cx, cy, cz;
+    curl_smoothed(g, S, fc, f.c[EX], f.c[EY], f.c[EZ], sm, s, sp, j, k, cx, cy, cz);
+    const size_t id = (size_t)s * nyz + r;
+    if (mode == 1) {
+      f.c[BX][id] = (f.c[BX][id] - fc.hdt * cc.c[0][id]) - fc.hdt * cx;
+      f.c[BY][id] = (f.c[BY][id] - fc.hdt * cc.c[1][id]) - fc.hdt * cy;
+      f.c[BZ][id] = (f.c[BZ][id] - fc.hdt * cc.c[2][id]) - fc.hdt * cz;
+    }
+    cc.c[0][id] = cx;
+    cc.c[1][id] = cy;
+    cc.c[2][id] = cz;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Gather + Boris push + position update + Esirkepov deposit, one thread per
 // particle; fields read from global memory, J accumulated with atomics.
 // ---------------------------------------------------------------------------

@@ -39,6 +39,16 @@ struct pic_t {
 
   // device memory
   void* fields = nullptr;   // 9 component arrays of ncell values
+  void* curl = nullptr;     // cached smoothed curl of E (3 arrays)
+  bool curl_valid = false;  // false: recompute before the next step
+  // tile-sorted particles
+  bool tiled = true;
+  pic::Tiles tiles = {1, 1, 1, 1, 1, 1, 1};
+  int* keys = nullptr;      // destination tile per particle
+  int* tstart[2] = {nullptr, nullptr};  // tile starts of pb[0], pb[1]
+  int* tcnt = nullptr;      // per-tile counts of the next buffer
+  int* tfill = nullptr;     // per-tile fill counters of the scatter
+  bool need_sort = false;   // particles not grouped by tile (after load/set)
   pic::PartBuf pb[2];       // current and compaction target
   int cur = 0;
   long long capacity = 0;

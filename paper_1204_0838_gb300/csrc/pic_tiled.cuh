@@ -1,0 +1,438 @@
+// pic_tiled.cuh -- tile-sorted particle kernels: particles are kept grouped
+// by cell tile; one CTA stages its tile's E/B (plus the cubic-stencil halo)
+// in shared memory, gathers, pushes, deposits J into a shared-memory tile and
+// flushes it with global atomics.  Re-binning after each step is a counting
+// sort by tile (count fused into the push, scan, scatter).
+#pragma once
+
+#include "pic_kernels.cuh"
+
+namespace pic {
+
+template <typename T>
+__device__ __forceinline__ int tile_of(const Geom<T>& g, const Tiles& tl, int cx, int cy, int cz) {
+  return ((cx / tl.tx) * tl.nty + cy / tl.ty) * tl.ntz + cz / tl.tz;
+}
+
+// Shared-memory extents: E/B staged over cells [c0-2, c0+t+2) per axis (the
+// half-staggered cubic gather reaches c-2 .. c+2), J over [c0-2, c0+t+3)
+// (the Esirkepov window of a particle that moves at most one cell reaches
+// c-2 .. c+3).
+__host__ __device__ __forceinline__ int stage_n(const Tiles& tl) { return (tl.tx + 4) * (tl.ty + 4) * (tl.tz + 4); }
+__host__ __device__ __forceinline__ int jtile_n(const Tiles& tl) { return (tl.tx + 5) * (tl.ty + 5) * (tl.tz + 5); }
+
+template <typename T>
+size_t tiled_smem_bytes(const Tiles& tl) {
+  return sizeof(T) * (6 * (size_t)stage_n(tl) + 3 * (size_t)jtile_n(tl));
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Warp-aggregated add of 1 to counter[key] for every lane with key >= 0;
+// returns this lane's rank among the lanes that share its key, and the
+// aggregated base offset through *base (only meaningful if want_base).
+// All 32 lanes must call it.
+__device__ __forceinline__ int warp_count(int* counter, int key, bool want_base, int* base) {
+  const unsigned m = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int b = 0;
+  if (lane == leader && key >= 0) b = want_base ? atomicAdd(counter + key, __popc(m)) : (atomicAdd(counter + key, __popc(m)), 0);
+  b = __shfl_sync(0xffffffffu, b, leader);
+  if (base) *base = b;
+  return __popc(m & lanemask_lt());
+}
+
+// Gather one field component from the staged tile: 4x4x4 separable sum,
+// contracting z first, then y, then x.
+template <typename T>
+__device__ __forceinline__ T gather_smem(const T* __restrict__ s, int SY, int SZ, int bx, int by, int bz,
+                                         const T* wx, const T* wy, const T* wz) {
+  T ax = T(0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    T ay = T(0);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const T* row = s + ((bx + a) * SY + (by + b)) * SZ + bz;
+      T az = row[0] * wz[0];
+      az = fma(row[1], wz[1], az);
+      az = fma(row[2], wz[2], az);
+      az = fma(row[3], wz[3], az);
+      ay = fma(az, wy[b], ay);
+    }
+    ax = fma(ay, wx[a], ax);
+  }
+  return ax;
+}
+
+// One CTA per tile.  keys[p] receives the particle's tile after the move (or
+// -1 when it leaves the open-x range once the window has moved to
+// origin_after); cnt_next[tile] counts the particles each tile will hold.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_push_tiled(Geom<T> g, Tiles tl, Fields<T> f, Parts<T> p,
+                                                   const int* __restrict__ tstart, int capacity,
+                                                   int* __restrict__ keys, int* __restrict__ cnt_next,
+                                                   T h, T q, int origin_after, int xlo, int xhi,
+                                                   unsigned long long* pushed, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int t = blockIdx.x;
+  const int pbeg = min(tstart[t], capacity), pend = min(tstart[t + 1], capacity);
+  if (pbeg >= pend) return;
+  const int tzi = t % tl.ntz, rest = t / tl.ntz;
+  const int tyi = rest % tl.nty, txi = rest / tl.nty;
+  const int o3[3] = {txi * tl.tx - 2, tyi * tl.ty - 2, tzi * tl.tz - 2};  // staged origin (cells)
+  const int SX = tl.tx + 4, SY = tl.ty + 4, SZ = tl.tz + 4;
+  const int JY = tl.ty + 5, JZ = tl.tz + 5;
+  const int nS = SX * SY * SZ, nJ = jtile_n(tl);
+  T* sF = sm;
+  T* sJ = sm + 6 * nS;
+
+  // stage E and B (wrapped storage indices; see the ring note in pic_device.cuh)
+  for (int i = threadIdx.x; i < nS; i += blockDim.x) {
+    const int lz = i % SZ, r = i / SZ;
+    const int ly = r % SY, lx = r / SY;
+    const size_t gi = (size_t)wrapi(o3[0] + lx, g.nx) * g.nyz + (size_t)wrapi(o3[1] + ly, g.ny) * g.nz +
+                      wrapi(o3[2] + lz, g.nz);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sF[c * nS + i] = f.c[c][gi];
+  }
+  for (int i = threadIdx.x; i < 3 * nJ; i += blockDim.x) sJ[i] = T(0);
+  if (threadIdx.x == 0) atomicAdd(pushed, (unsigned long long)(pend - pbeg));
+  __syncthreads();
+
+  const int N[3] = {g.nx, g.ny, g.nz};
+  const T dtd[3] = {g.dt / g.dx, g.dt / g.dy, g.dt / g.dz};
+  const T jc[3] = {T(-1) / (g.dt * g.dy * g.dz), T(-1) / (g.dt * g.dx * g.dz), T(-1) / (g.dt * g.dx * g.dy)};
+  const T third = T(1) / T(3);
+
+  for (int base = pbeg; base < pend; base += blockDim.x) {
+    const int pi = base + threadIdx.x;
+    int key = -2;
+    if (pi < pend) {
+      const int cell = p.cell[pi];
+      int c0[3];
+      c0[0] = cell / g.nyz;
+      const int rem = cell - c0[0] * g.nyz;
+      c0[1] = rem / g.nz;
+      c0[2] = rem - c0[1] * g.nz;
+      int lc[3];
+      T o0[3], u[3];
+      const int text[3] = {tl.tx, tl.ty, tl.tz};
+      bool inside = true;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        lc[d] = c0[d] - o3[d];  // in [2, t+2) for a particle of this tile
+        inside = inside && lc[d] >= 2 && lc[d] < text[d] + 2;
+        o0[d] = p.o[d][pi];
+        u[d] = p.u[d][pi];
+      }
+      if (!inside) {  // never expected: keeps every shared-memory index in range
+        atomicOr(err, 4);
+        keys[pi] = -1;
+        key = -1;
+      } else {
+      T wn[3][4], wh[3][4];
+      int bn[3], bh[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        bspline3(o0[d], wn[d]);
+        const bool lo = o0[d] < T(0.5);
+        bspline3(lo ? o0[d] + T(0.5) : o0[d] - T(0.5), wh[d]);
+        bn[d] = lc[d] - 1;
+        bh[d] = lc[d] - (lo ? 2 : 1);
+      }
+      T E[3], B[3];
+      E[0] = gather_smem(sF + 0 * nS, SY, SZ, bh[0], bn[1], bn[2], wh[0], wn[1], wn[2]);
+      E[1] = gather_smem(sF + 1 * nS, SY, SZ, bn[0], bh[1], bn[2], wn[0], wh[1], wn[2]);
+      E[2] = gather_smem(sF + 2 * nS, SY, SZ, bn[0], bn[1], bh[2], wn[0], wn[1], wh[2]);
+      B[0] = gather_smem(sF + 3 * nS, SY, SZ, bn[0], bh[1], bh[2], wn[0], wh[1], wh[2]);
+      B[1] = gather_smem(sF + 4 * nS, SY, SZ, bh[0], bn[1], bh[2], wh[0], wn[1], wh[2]);
+      B[2] = gather_smem(sF + 5 * nS, SY, SZ, bh[0], bh[1], bn[2], wh[0], wh[1], wn[2]);
+
+      // relativistic Boris push
+      T um[3], tv[3], sv[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) um[d] = u[d] + h * E[d];
+      const T gm = sqrt(T(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+      const T hg = h / gm;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) tv[d] = hg * B[d];
+      const T s2 = T(2) / (T(1) + tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) sv[d] = s2 * tv[d];
+      const T px = um[0] + (um[1] * tv[2] - um[2] * tv[1]);
+      const T py = um[1] + (um[2] * tv[0] - um[0] * tv[2]);
+      const T pz = um[2] + (um[0] * tv[1] - um[1] * tv[0]);
+      u[0] = um[0] + (py * sv[2] - pz * sv[1]) + h * E[0];
+      u[1] = um[1] + (pz * sv[0] - px * sv[2]) + h * E[1];
+      u[2] = um[2] + (px * sv[1] - py * sv[0]) + h * E[2];
+      const T ig = T(1) / sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+
+      // position update (cell + offset), |move| < 1 cell per axis
+      T o1[3];
+      int dc[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T o = o0[d] + dtd[d] * u[d] * ig;
+        int k = 0;
+        if (o < T(0)) {
+          o += T(1);
+          k = -1;
+        } else if (o >= T(1)) {
+          o -= T(1);
+          k = 1;
+        }
+        if (o >= T(1)) {
+          o = T(0);
+          k += 1;
+        }
+        o1[d] = o;
+        dc[d] = k;
+      }
+
+      // Esirkepov deposit into the shared J tile: 5-node window per axis
+      // starting at c0 - 1 + min(dc, 0); S0 on window nodes p0..p0+3, S1 on
+      // p1..p1+3.  Wx(i,j,k) = DSx(i) A(j,k) with A = S0y S0z + DSy S0z/2 +
+      // S0y DSz/2 + DSy DSz/3 = S0y (S0z + DSz/2) + DSy (S0z/2 + DSz/3).
+      T S0[3][5], DS[3][5];
+      int lw[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T w1[4];
+        bspline3(o1[d], w1);
+        const int p0 = dc[d] < 0 ? 1 : 0, p1 = dc[d] > 0 ? 1 : 0;
+        lw[d] = lc[d] - 1 - p0;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+          const T a0 = p0 ? (m > 0 ? wn[d][m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? wn[d][m < 4 ? m : 3] : T(0));
+          const T a1 = p1 ? (m > 0 ? w1[m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? w1[m < 4 ? m : 3] : T(0));
+          S0[d][m] = a0;
+          DS[d][m] = a1 - a0;
+        }
+      }
+      const T qw = q * p.w[pi];
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) {
+        // axis `comp` carries the running sum; (b, c) are the other two axes
+        const int ab = comp == 0 ? 1 : 0, ac = comp == 2 ? 1 : 2;
+        T P[4];
+        T run = T(0);
+        const T cf = qw * jc[comp];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          run += DS[comp][m];
+          P[m] = cf * run;
+        }
+        T ak[5], bk[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+          ak[m] = S0[ac][m] + T(0.5) * DS[ac][m];
+          bk[m] = T(0.5) * S0[ac][m] + third * DS[ac][m];
+        }
+        T* J = sJ + comp * nJ;
+        // strides of the three axes in the J tile; (m, b, c) walk (comp, ab, ac)
+        const int st[3] = {JY * JZ, JZ, 1};
+        const int base0 = lw[0] * st[0] + lw[1] * st[1] + lw[2] * st[2];
+        const int sm_ = st[comp], sb_ = st[ab], sc_ = st[ac];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          const T sb = S0[ab][b], db = DS[ab][b];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            const T A = sb * ak[c] + db * bk[c];
+            if (A != T(0)) {
+#pragma unroll
+              for (int m = 0; m < 4; ++m) {
+                const T v = P[m] * A;
+                if (v != T(0)) atomicAdd(J + base0 + m * sm_ + b * sb_ + c * sc_, v);
+              }
+            }
+          }
+        }
+      }
+
+      // store in place; the key is the destination tile (or -1: absorbed)
+      const int n0 = wrapi(c0[0] + dc[0], N[0]);
+      const int n1 = wrapi(c0[1] + dc[1], N[1]);
+      const int n2 = wrapi(c0[2] + dc[2], N[2]);
+      p.cell[pi] = n0 * g.nyz + n1 * g.nz + n2;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        p.o[d][pi] = o1[d];
+        p.u[d][pi] = u[d];
+      }
+      key = tile_of(g, tl, n0, n1, n2);
+      if (!g.periodic_x) {
+        int rel = n0 - origin_after;
+        if (rel < 0) rel += g.nx;
+        if (rel < xlo || rel > xhi) key = -1;
+      }
+      keys[pi] = key;
+      }
+    }
+    warp_count(cnt_next, key, false, nullptr);
+  }
+  __syncthreads();
+
+  // flush the J tile (cells [o3, o3 + t + 5) per axis, wrapped)
+  for (int i = threadIdx.x; i < 3 * nJ; i += blockDim.x) {
+    const T v = sJ[i];
+    if (v == T(0)) continue;
+    const int comp = i / nJ, li = i - comp * nJ;
+    const int lz = li % JZ, r = li / JZ;
+    const int ly = r % JY, lx = r / JY;
+    const size_t gi = (size_t)wrapi(o3[0] + lx, g.nx) * g.nyz + (size_t)wrapi(o3[1] + ly, g.ny) * g.nz +
+                      wrapi(o3[2] + lz, g.nz);
+    atomicAdd(f.c[JX + comp] + gi, v);
+  }
+}
+
+// Keys from the current cells (used after loading or set_particles).
+template <typename T>
+__global__ void k_keys(Geom<T> g, Tiles tl, Parts<T> p, const int* __restrict__ d_np, int* keys, int* cnt) {
+  const int n = *d_np;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int pi = base + threadIdx.x;
+    int key = -2;
+    if (pi < n) {
+      const int cell = p.cell[pi];
+      const int cx = cell / g.nyz, r = cell - cx * g.nyz;
+      key = tile_of(g, tl, cx, r / g.nz, r - (r / g.nz) * g.nz);
+      keys[pi] = key;
+    }
+    warp_count(cnt, key, false, nullptr);
+  }
+}
+
+// Exclusive scan of the tile counts into tile starts (single CTA of 1024
+// threads, contiguous chunk per thread).  Starts are clamped to the capacity;
+// a total above it sets the capacity error bit.
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int* __restrict__ cnt, int* __restrict__ tstart, int n,
+                                                    int* d_np_out, int capacity, int* err) {
+  __shared__ long long part[1024];
+  const int tid = threadIdx.x;
+  const int chunk = (n + 1023) / 1024;
+  const int b = min(tid * chunk, n), e = min(b + chunk, n);
+  long long s = 0;
+  for (int i = b; i < e; ++i) s += cnt[i];
+  part[tid] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    long long v = tid >= off ? part[tid - off] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  long long run = part[tid] - s;  // exclusive prefix of this chunk
+  for (int i = b; i < e; ++i) {
+    tstart[i] = (int)min(run, (long long)capacity);
+    run += cnt[i];
+  }
+  if (tid == 1023) {
+    const long long total = part[1023];
+    tstart[n] = (int)min(total, (long long)capacity);
+    *d_np_out = (int)min(total, (long long)capacity);
+    if (total > capacity) atomicOr(err, 1);
+  }
+}
+
+// Scatter the kept particles into their tiles of the other buffer.
+template <typename T>
+__global__ void k_scatter(Parts<T> src, const int* __restrict__ keys, const int* __restrict__ d_np_src,
+                          Parts<T> dst, const int* __restrict__ tstart, int* fill, int* err) {
+  const int n = *d_np_src;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int pi = base + threadIdx.x;
+    const int key = pi < n ? keys[pi] : -2;
+    int off;
+    const int rank = warp_count(fill, key, true, &off);
+    if (key >= 0) {
+      const int slot = tstart[key] + off + rank;
+      if (slot >= tstart[key + 1]) {
+        atomicOr(err, 2);
+        continue;
+      }
+      dst.cell[slot] = src.cell[pi];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        dst.o[d][slot] = src.o[d][pi];
+        dst.u[d][slot] = src.u[d][pi];
+      }
+      dst.w[slot] = src.w[pi];
+      if (dst.id) dst.id[slot] = src.id[pi];
+    }
+  }
+}
+
+// Window injection into a tile-sorted buffer: pass 0 counts per tile into
+// cnt, pass 1 places the particles with the tile fill counters.  The draws
+// are the same counter-based SplitMix64 keys as plain loading, so both
+// passes regenerate identical particles.
+template <typename T>
+__global__ void k_inject_tiled(Geom<T> g, Tiles tl, Parts<T> p, LoadSpec L, int pass, int* cnt,
+                               const int* __restrict__ tstart, int* fill, int* err) {
+  const long long nslot = (long long)(L.hi - L.lo + 1) * g.nyz * L.ppc;
+  for (long long q0 = (long long)blockIdx.x * blockDim.x; q0 < nslot; q0 += (long long)gridDim.x * blockDim.x) {
+    const long long qq = q0 + threadIdx.x;
+    int key = -2;
+    double o[3] = {0, 0, 0}, n = 0;
+    int sx = 0, j = 0, k = 0, sl = 0;
+    unsigned long long cell = 0;
+    if (qq < nslot) {
+      sl = (int)(qq % L.ppc);
+      const long long c = qq / L.ppc;
+      const int r = (int)(c % g.nyz);
+      const int ci = L.lo + (int)(c / g.nyz);
+      j = r / g.nz;
+      k = r - j * g.nz;
+      const long long lab = L.shifts + ci;
+      cell = ((unsigned long long)lab * g.ny + j) * g.nz + k;
+      const unsigned long long ctr = (cell * L.ppc + sl) * 3ull;
+      double rr[3];
+      for (int d = 0; d < 3; ++d) rr[d] = unit_uniform(L.seed, ctr + d);
+      if (L.lattice) {
+        const int ix = sl / (L.ns[1] * L.ns[2]), iy = (sl / L.ns[2]) % L.ns[1], iz = sl % L.ns[2];
+        o[0] = (ix + rr[0]) / L.ns[0];
+        o[1] = (iy + rr[1]) / L.ns[1];
+        o[2] = (iz + rr[2]) / L.ns[2];
+      } else {
+        o[0] = rr[0];
+        o[1] = rr[1];
+        o[2] = rr[2];
+      }
+      n = profile_at(L.px, L.pn, L.np, L.x0 + ((double)lab + o[0]) * L.dx);
+      sx = slab_of(g, ci);
+      if (n > 0.0) key = tile_of(g, tl, sx, j, k);
+    }
+    if (pass == 0) {
+      warp_count(cnt, key, false, nullptr);
+      continue;
+    }
+    int off;
+    const int rank = warp_count(fill, key, true, &off);
+    if (key >= 0) {
+      const int slot = tstart[key] + off + rank;
+      if (slot >= tstart[key + 1]) {
+        atomicOr(err, 2);
+        continue;
+      }
+      p.cell[slot] = sx * g.nyz + j * g.nz + k;
+      for (int d = 0; d < 3; ++d) {
+        T od = (T)o[d];
+        if (od >= T(1)) od = one_below<T>();
+        p.o[d][slot] = od;
+        p.u[d][slot] = T(0);
+      }
+      p.w[slot] = (T)(n * L.dVppc);
+      if (p.id) p.id[slot] = (uint32_t)(cell * L.ppc + sl);
+    }
+  }
+}
+
+}  // namespace pic

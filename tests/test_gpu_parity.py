@@ -77,14 +77,36 @@ def test_plane_wave_exact_shift_on_gpu():
 # ---------------------------------------------------------------------------
 # one full step with random particles and fields
 # ---------------------------------------------------------------------------
+@pytest.fixture(params=["tiled", "simple"])
+def kernel(request, monkeypatch):
+    if request.param == "simple":
+        monkeypatch.setenv("PIC_KERNEL", "simple")
+    else:
+        monkeypatch.delenv("PIC_KERNEL", raising=False)
+    return request.param
+
+
 @pytest.mark.parametrize("periodic,shape,npart", [(True, (32, 16, 16), 20000),
                                                   (False, (48, 16, 8), 20000),
                                                   (True, (16, 4, 4), 3000)])
-def test_one_step_parity_random_state(periodic, shape, npart):
+def test_one_step_parity_random_state(periodic, shape, npart, kernel):
     g, o = _pair(shape, periodic)
     _set_random(g, o, shape, npart, seed=2, periodic=periodic)
     g.step(1)
     o.step(1)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+
+
+@pytest.mark.parametrize("tile", ["5,3,3", "16,4,8", "1,1,1", "32,16,16"])
+def test_ragged_and_odd_tiles(tile, monkeypatch):
+    monkeypatch.setenv("PIC_TILE", tile)
+    shape = (37, 11, 13)
+    g, o = _pair(shape, False)
+    _set_random(g, o, shape, 8000, seed=6, periodic=False)
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
     compare_particles(g.particles(), o.particles(), 1e-10)
     compare_fields(g, o, 1e-10)
 
@@ -100,7 +122,7 @@ def test_one_step_parity_c0_size():
     compare_fields(g, o, 1e-10)
 
 
-def test_absorbing_boundary_drops_same_particles():
+def test_absorbing_boundary_drops_same_particles(kernel):
     shape = (32, 8, 8)
     g, o = _pair(shape, False)
     _set_random(g, o, shape, 5000, seed=4, periodic=False, umax=20.0)
