@@ -159,8 +159,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_push_tiled(Geom
       T um[3], tv[3], sv[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) um[d] = u[d] + h * E[d];
-      const T gm = sqrt(T(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-      const T hg = h / gm;
+      const T hg = h * rsqrt(T(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);  // h / gamma-
 #pragma unroll
       for (int d = 0; d < 3; ++d) tv[d] = hg * B[d];
       const T s2 = T(2) / (T(1) + tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2]);
@@ -172,7 +171,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_push_tiled(Geom
       u[0] = um[0] + (py * sv[2] - pz * sv[1]) + h * E[0];
       u[1] = um[1] + (pz * sv[0] - px * sv[2]) + h * E[1];
       u[2] = um[2] + (px * sv[1] - py * sv[0]) + h * E[2];
-      const T ig = T(1) / sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      const T ig = rsqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);  // 1 / gamma
 
       // position update (cell + offset), |move| < 1 cell per axis
       T o1[3];
@@ -200,14 +199,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_push_tiled(Geom
       // starting at c0 - 1 + min(dc, 0); S0 on window nodes p0..p0+3, S1 on
       // p1..p1+3.  Wx(i,j,k) = DSx(i) A(j,k) with A = S0y S0z + DSy S0z/2 +
       // S0y DSz/2 + DSy DSz/3 = S0y (S0z + DSz/2) + DSy (S0z/2 + DSz/3).
+      // A particle that stays in its cell along an axis has a 4-node support
+      // there (node 5 of the window carries nothing): nw = 4 or 5 nodes, and
+      // the running sum along the current's own axis vanishes on its last
+      // node, so only nw - 1 current values are nonzero.
       T S0[3][5], DS[3][5];
-      int lw[3];
+      int lw[3], nw[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         T w1[4];
         bspline3(o1[d], w1);
         const int p0 = dc[d] < 0 ? 1 : 0, p1 = dc[d] > 0 ? 1 : 0;
         lw[d] = lc[d] - 1 - p0;
+        nw[d] = dc[d] != 0 ? 5 : 4;
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
           const T a0 = p0 ? (m > 0 ? wn[d][m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? wn[d][m < 4 ? m : 3] : T(0));
@@ -240,17 +244,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_push_tiled(Geom
         const int st[3] = {JY * JZ, JZ, 1};
         const int base0 = lw[0] * st[0] + lw[1] * st[1] + lw[2] * st[2];
         const int sm_ = st[comp], sb_ = st[ab], sc_ = st[ac];
+        const int nm = nw[comp] - 1, nb = nw[ab], nc = nw[ac];
 #pragma unroll
         for (int b = 0; b < 5; ++b) {
-          const T sb = S0[ab][b], db = DS[ab][b];
+          if (b < nb) {
+            const T sb = S0[ab][b], db = DS[ab][b];
 #pragma unroll
-          for (int c = 0; c < 5; ++c) {
-            const T A = sb * ak[c] + db * bk[c];
-            if (A != T(0)) {
+            for (int c = 0; c < 5; ++c) {
+              if (c < nc) {
+                const T A = sb * ak[c] + db * bk[c];
 #pragma unroll
-              for (int m = 0; m < 4; ++m) {
-                const T v = P[m] * A;
-                if (v != T(0)) atomicAdd(J + base0 + m * sm_ + b * sb_ + c * sc_, v);
+                for (int m = 0; m < 4; ++m)
+                  if (m < nm) atomicAdd(J + base0 + m * sm_ + b * sb_ + c * sc_, P[m] * A);
               }
             }
           }
