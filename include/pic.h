@@ -210,6 +210,26 @@ int pic_timing_read(pic_t* h, pic_timing* out);
 
 int pic_destroy(pic_t* h);
 
+/* ---- diagnostics that allocate nothing ----
+ * The paper has no counterpart to this call; it serves callers of the
+ * library.  pic_diag may allocate device scratch (through cudaMalloc or the
+ * pic_alloc hooks) the first time a diagnostic is requested.  Callers that
+ * must not allocate after set-up -- a host framework with a fixed device
+ * memory budget, a latency-critical loop where cudaMalloc/cudaFree would
+ * synchronise the device, code running inside another library's callbacks --
+ * use pic_diag_noalloc instead: same kinds, arguments, units and results as
+ * pic_diag, with the reduction scratch in a fixed file-scope device array of
+ * PIC_NOALLOC_MAX_LEN doubles (512 KiB, present on every GPU that loads the
+ * library until it is unloaded).  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Results longer than PIC_NOALLOC_MAX_LEN values (a
+ * lineout of nx > 65536 cells, a spectrum of more bins) return PIC_ERR_ARG.
+ * The first call made with a given device current looks up the array's
+ * device address (cudaGetSymbolAddress) once for that device; make that first
+ * call before any stream capture.  All calls share the array: each call
+ * clears the part it uses, and calls that overlap on the GPU race on it. */
+#define PIC_NOALLOC_MAX_LEN 65536
+int pic_diag_noalloc(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* a);
+
 /* ---- batched instances (a0 / density scans) ----
  * A batch borrows n FP32 handles (they must outlive it and may not be stepped
  * on their own while batched) and advances them together: per step one CUDA

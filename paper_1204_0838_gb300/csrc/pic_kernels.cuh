@@ -535,7 +535,7 @@ __global__ void k_load(Geom<T> g, Parts<T> p, int* d_np, int* d_err, LoadSpec L)
 
 // After loading or injection the counter may exceed the capacity (the
 // overflowing particles were not written and the error bit is set): clamp it.
-__global__ void k_clamp_count(int* d_np, int capacity) {
+static __global__ void k_clamp_count(int* d_np, int capacity) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && *d_np > capacity) *d_np = capacity;
 }
 

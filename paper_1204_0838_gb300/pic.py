@@ -96,6 +96,8 @@ _SIGS = {
     "pic_get_particles": (C.c_int, [C.c_void_p, C.POINTER(pic_particles)]),
     "pic_set_particles": (C.c_int, [C.c_void_p, C.POINTER(pic_particles)]),
     "pic_destroy": (C.c_int, [C.c_void_p]),
+    "pic_diag_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_size_t,
+                                   C.POINTER(pic_diag_args)]),
     "pic_timing_start": (C.c_int, [C.c_void_p, C.c_int]),
     "pic_timing_read": (C.c_int, [C.c_void_p, C.POINTER(pic_timing)]),
     "pic_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
@@ -214,6 +216,14 @@ def pic_diag(h, kind, length=1, gamma_min=0.0, e_min=0.0, e_max=0.0):
     out = np.zeros(max(int(length), 1))
     a = pic_diag_args(float(gamma_min), float(e_min), float(e_max))
     _check(lib().pic_diag(h, int(kind), _dp(out), out.size, C.byref(a)), "pic_diag", h)
+    return out
+
+
+def pic_diag_noalloc(h, kind, length=1, gamma_min=0.0, e_min=0.0, e_max=0.0):
+    """pic_diag without any device allocation (scratch in a fixed device array)."""
+    out = np.zeros(max(int(length), 1))
+    a = pic_diag_args(float(gamma_min), float(e_min), float(e_max))
+    _check(lib().pic_diag_noalloc(h, int(kind), _dp(out), out.size, C.byref(a)), "pic_diag_noalloc", h)
     return out
 
 
