@@ -28,9 +28,12 @@ if ROOT not in sys.path:
 
 METRIC = "particle-steps/s (cubic gather+Boris+deposit+field), FP32/batched vs FP64, 1 GB300"
 UNIT = "particle-steps/s"
-# algorithmic cost per particle push of the gather/push/deposit kernel
-FLOP_PER_PARTICLE = 2496  # counted operation by operation in the design doc
-BYTES_PER_PARTICLE = {"fp64": 120, "fp32": 60}  # read + write of the SoA record
+# Algorithmic cost of one particle push (gather + Boris + position + Esirkepov
+# deposit), counted operation by operation for the minimal formulation with a
+# 4-node support per axis (a particle that crosses a cell face needs more):
+# weights 138, gather 882, Boris 54, position 17, deposit 522 (FMA = 2 flop).
+FLOP_PER_PARTICLE = 1613
+BYTES_PER_PARTICLE = {"fp64": 112, "fp32": 60}  # SoA record read once, written once
 
 
 def _args():
