@@ -42,7 +42,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c4"])
+    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--instances", type=int, default=32, help="c3: batched instances")
     ap.add_argument("--start-step", type=int, default=-1)
     ap.add_argument("--crop", default="", help="nx,ny,nz (profiling small cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -60,7 +61,7 @@ def _workload(args):
     from paper_1204_0838_gb300 import workloads as W
     start = args.start_step
     if start < 0:
-        start = {"c0": 0, "c1": 900, "c2": 900, "c4": 4500}[args.config]
+        start = {"c0": 0, "c1": 900, "c2": 900, "c3": 450, "c4": 4500}[args.config]
     crop = tuple(int(v) for v in args.crop.split(",")) if args.crop else None
     cfg = W.config(args.config, crop=crop, start_step=start)
     return cfg, start
@@ -320,10 +321,111 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """c3: N uneven FP32 instances (a0, density, waist, grid scan) advanced
+    together, one CUDA graph launch per step; tile shapes autotuned."""
+    import torch
+    from paper_1204_0838_gb300 import build as pb
+    from paper_1204_0838_gb300 import pic, workloads as W
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    pb.build()
+    start = args.start_step if args.start_step >= 0 else 450
+    cfgs = W.batch_configs(args.instances, seed=W.DEFAULT_SEED + 1000 * rank)
+    sims, tiles = [], []
+    pushed_k2 = k2_ms = 0.0
+    cache = os.environ.get("PIC_AUTOTUNE_CACHE", "/tmp/pic_autotune_%d.json" % os.getpid())
+    for c in cfgs:
+        c = dict(c)
+        c["x0"] += start * c["dx"]
+        c["t_peak"] -= start * c["dx"] / W.C0
+        g = pic.Sim(c["nx"], c["ny"], c["nz"], c["dx"], c["dy"], c["dz"], c["lambda0"], x0=c["x0"],
+                    periodic_x=False, precision="fp32", seed=c["seed"], window=c["window"])
+        g.add_species(c["prof_x"], c["prof_n"], c["ppc"], loading=c["loading"])
+        g.add_laser(c["a0"], c["waist"], c["fwhm"], c["lambda0"], c["x_focus"], c["t_peak"])
+        tile, _ = pic.pic_autotune(g.h, 1, cache)
+        tiles.append(tile)
+        # one host-driven step per member with kernel timing: the roofline of the push kernel
+        p0 = g.info()["pushed"]
+        pic.pic_timing_start(g.h, True)
+        g.step(1)
+        t = pic.pic_timing_read(g.h)
+        pic.pic_timing_start(g.h, False)
+        k2_ms += t["ms"]["gather_push_deposit"]
+        pushed_k2 += g.info()["pushed"] - p0
+        sims.append(g)
+    b = pic.pic_batch_create([g.h for g in sims])
+    pic.pic_batch_step(b, max(args.warmup, 1))
+    p0 = sum(g.info()["pushed"] for g in sims)
+    clocks = Clocks(local)
+    clocks.start()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    g0 = pic.pic_batch_info(b)["graph_launches"]
+    k0 = pic.pic_batch_info(b)["kernel_launches"]
+    pic.pic_batch_step(b, args.steps)
+    info = pic.pic_batch_info(b)
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = info["last_step_ms"]
+    pushed = sum(g.info()["pushed"] for g in sims) - p0
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+        c = torch.tensor([float(pushed)], dtype=torch.float64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        pushed = float(c[0])
+    value = pushed / (ms / 1e3)
+    t0 = time.perf_counter()
+    pe0 = sum(g.info()["pushed"] for g in sims)
+    for _ in range(args.steps):
+        pic.pic_batch_step(b, 1)
+        pic.pic_batch_diag(b, 0, pic.PIC_DIAG_FIELD_ENERGY)
+    e2e = (sum(g.info()["pushed"] for g in sims) - pe0) / (time.perf_counter() - t0)
+    peaks, src = _peaks()
+    achieved = FLOP_PER_PARTICLE * pushed_k2 / (k2_ms / 1e3) / 1e12 if k2_ms > 0 else 0.0
+    peak = _fp_peak_tflops("fp32", peaks.get("sm_max_mhz", 2070.0))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c3: %d FP32 instances, a0 U[2,5], n U[0.003,0.02] n_c, waist "
+                                   "U[10,20] um, nx 256..768 x ny=nz 64..128, dx=lambda0/16, "
+                                   "dy=dz=lambda0/3, 1-2 ppc, window at c, steps %d.. of 500; one "
+                                   "CUDA graph launch per step; autotuned tiles" % (len(sims), start),
+                       "tiles": tiles, "cells": int(sum(c["nx"] * c["ny"] * c["nz"] for c in cfgs)),
+                       "l2": "inputs larger than L2, no flush"},
+            "particles": int(sum(g.info()["np"] for g in sims)),
+            "roofline": {"kernel": "k_push_tiled (FP32), one host-driven step per member",
+                         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x max clock"},
+            "clocks": clk,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8,
+                    "note": "pic_batch_step(1) + pic_batch_diag(field energy of instance 0) per step"},
+            "gpu_launches": info["kernel_launches"] - k0,
+            "graph_launches": info["graph_launches"] - g0}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pic.pic_batch_destroy(b)
+    for g in sims:
+        g.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "c3":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -230,12 +230,34 @@ int pic_destroy(pic_t* h);
 #define PIC_NOALLOC_MAX_LEN 65536
 int pic_diag_noalloc(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* a);
 
+/* ---- tile shape and its autotuner ----
+ * Particles are kept sorted by cell tile; one CTA works on one tile with its
+ * E/B halo and J tile in shared memory.  pic_set_tiles picks the tile shape
+ * (cells per axis; shrunk to the grid).  pic_autotune times a set of
+ * candidate shapes on `steps` trial steps each, restoring the state after
+ * every trial (the simulation does not advance), keeps the fastest and
+ * returns it (tile_out[3], ms_out per step; either may be NULL).  With a
+ * cache file (cache_path, else $PIC_AUTOTUNE_CACHE, else none) the choice is
+ * read from / written to a JSON object keyed by precision, ppc and grid. */
+int pic_set_tiles(pic_t* h, int tx, int ty, int tz);
+int pic_autotune(pic_t* h, int steps, const char* cache_path, int* tile_out, double* ms_out);
+
 /* ---- batched instances (a0 / density scans) ----
- * A batch borrows n FP32 handles (they must outlive it and may not be stepped
- * on their own while batched) and advances them together: per step one CUDA
- * graph launch whose kernels each cover every instance's work. */
+ * A batch borrows n FP32 handles with tile-sorted particles (they must
+ * outlive it and may not be stepped on their own while batched; boundary
+ * laser sources are not supported) and advances them together.  The step of
+ * every member is captured once into a CUDA graph (members on forked streams
+ * so that small instances run concurrently; every step parameter, including
+ * the FP64 window accumulator and the ring origin, is read from device
+ * memory), and each step is one graph launch.  Graphs are re-captured when a
+ * member's particle buffers grow. */
 int pic_batch_create(int n, pic_t* const* sims, pic_batch_t** out);
 int pic_batch_step(pic_batch_t* b, int n);
+/* graph launches and kernel launches issued by the batch since creation, and
+ * the device time of the last pic_batch_step call (CUDA events on the batch
+ * stream around its graph launches), in ms; any pointer may be NULL. */
+int pic_batch_info(const pic_batch_t* b, int64_t* graph_launches, int64_t* kernel_launches,
+                   double* last_step_ms);
 int pic_batch_diag(pic_batch_t* b, int instance, int kind, double* out, size_t len,
                    const pic_diag_args* a);
 int pic_batch_destroy(pic_batch_t* b);

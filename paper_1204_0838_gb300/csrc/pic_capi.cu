@@ -123,6 +123,8 @@ Geom<T> geom(const pic_t* h) {
   g.dx = (T)h->dx;
   g.dy = (T)h->dy;
   g.dz = (T)h->dz;
+  g.dyn = nullptr;
+  g.gate = 0;
   return g;
 }
 
@@ -769,15 +771,18 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
   h->tstart[1] = (int*)dalloc(h, sizeof(int) * (h->tiles.n + 1));
   h->tcnt = (int*)dalloc(h, sizeof(int) * h->tiles.n);
   h->tfill = (int*)dalloc(h, sizeof(int) * h->tiles.n);
+  h->tiles_alloc = h->tiles.n;
   if (!h->curl || !h->tstart[0] || !h->tstart[1] || !h->tcnt || !h->tfill) {
     pic_destroy(h);
     return PIC_ERR_OOM;
   }
   {
-    const size_t sm = h->precision == PIC_FP64 ? tiled_smem_bytes<double>(h->tiles) : tiled_smem_bytes<float>(h->tiles);
+    // the limit is a property of the kernel, shared by every handle: allow the
+    // largest tile any handle may pick (227 KB); each launch asks for its own
+    const int sm = 227 * 1024;
     cudaError_t e = h->precision == PIC_FP64
-                        ? cudaFuncSetAttribute(k_push_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                        : cudaFuncSetAttribute(k_push_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                        ? cudaFuncSetAttribute(k_push_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)
+                        : cudaFuncSetAttribute(k_push_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) {
       cudaGetLastError();
       pic_destroy(h);
@@ -1138,11 +1143,436 @@ int pic_destroy(pic_t* h) {
 }  // extern "C"
 
 // ===========================================================================
-// Batched instances: a batch borrows FP32 handles and advances them together.
+// Tile shapes and the autotuner
+// ===========================================================================
+namespace {
+
+int set_tiles(pic_t* h, int tx, int ty, int tz) {
+  const int n3[3] = {h->nx, h->ny, h->nz};
+  int t3[3] = {tx, ty, tz};
+  for (int d = 0; d < 3; ++d) t3[d] = std::max(1, std::min(t3[d], n3[d]));
+  Tiles tl;
+  tl.tx = t3[0];
+  tl.ty = t3[1];
+  tl.tz = t3[2];
+  tl.ntx = (h->nx + tl.tx - 1) / tl.tx;
+  tl.nty = (h->ny + tl.ty - 1) / tl.ty;
+  tl.ntz = (h->nz + tl.tz - 1) / tl.tz;
+  tl.n = tl.ntx * tl.nty * tl.ntz;
+  const size_t sm = h->precision == PIC_FP64 ? tiled_smem_bytes<double>(tl) : tiled_smem_bytes<float>(tl);
+  if (sm > 227 * 1024) return fail(h, PIC_ERR_ARG, "tile too large for shared memory");
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (tl.n > h->tiles_alloc) {
+    int* a0 = (int*)dalloc(h, sizeof(int) * (tl.n + 1));
+    int* a1 = (int*)dalloc(h, sizeof(int) * (tl.n + 1));
+    int* c = (int*)dalloc(h, sizeof(int) * tl.n);
+    int* f = (int*)dalloc(h, sizeof(int) * tl.n);
+    if (!a0 || !a1 || !c || !f) return fail(h, PIC_ERR_OOM, "tile arrays");
+    dfree(h, h->tstart[0]);
+    dfree(h, h->tstart[1]);
+    dfree(h, h->tcnt);
+    dfree(h, h->tfill);
+    h->tstart[0] = a0;
+    h->tstart[1] = a1;
+    h->tcnt = c;
+    h->tfill = f;
+    h->tiles_alloc = tl.n;
+  }
+  h->tiles = tl;
+  h->need_sort = true;
+  return PIC_OK;
+}
+
+// Device copy of the state that a trial step changes.
+struct Snapshot {
+  void* fields = nullptr;
+  void* curl = nullptr;
+  void* part = nullptr;
+  int ctrl[6];
+  int cur = 0;
+  int64_t step = 0, shifts = 0;
+  int origin = 0;
+  double win_frac = 0;
+  bool curl_valid = false, need_sort = false;
+  int np = 0;
+};
+
+int snapshot_take(pic_t* h, Snapshot* sn) {
+  const size_t es = esize(h);
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaMemcpy(sn->ctrl, h->d_ctrl, sizeof(sn->ctrl), cudaMemcpyDeviceToHost));
+  sn->np = sn->ctrl[h->cur];
+  sn->fields = dalloc(h, NCOMP * h->ncell * es);
+  sn->curl = dalloc(h, 3 * h->ncell * es);
+  const size_t per = 4 + 7 * es + (h->pb[0].id ? 4 : 0);
+  sn->part = dalloc(h, per * (size_t)std::max(sn->np, 1));
+  if (!sn->fields || !sn->curl || !sn->part) return fail(h, PIC_ERR_OOM, "autotune snapshot");
+  CK(h, cudaMemcpyAsync(sn->fields, h->fields, NCOMP * h->ncell * es, cudaMemcpyDeviceToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(sn->curl, h->curl, 3 * h->ncell * es, cudaMemcpyDeviceToDevice, h->stream));
+  const PartBuf& b = h->pb[h->cur];
+  char* dst = (char*)sn->part;
+  const size_t n = sn->np;
+  CK(h, cudaMemcpyAsync(dst, b.cell, 4 * n, cudaMemcpyDeviceToDevice, h->stream));
+  dst += 4 * n;
+  for (int d = 0; d < 3; ++d, dst += es * n) CK(h, cudaMemcpyAsync(dst, b.o[d], es * n, cudaMemcpyDeviceToDevice, h->stream));
+  for (int d = 0; d < 3; ++d, dst += es * n) CK(h, cudaMemcpyAsync(dst, b.u[d], es * n, cudaMemcpyDeviceToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(dst, b.w, es * n, cudaMemcpyDeviceToDevice, h->stream));
+  dst += es * n;
+  if (b.id) CK(h, cudaMemcpyAsync(dst, b.id, 4 * n, cudaMemcpyDeviceToDevice, h->stream));
+  sn->cur = h->cur;
+  sn->step = h->step;
+  sn->shifts = h->shifts;
+  sn->origin = h->origin;
+  sn->win_frac = h->win_frac;
+  sn->curl_valid = h->curl_valid;
+  sn->need_sort = h->need_sort;
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+// Restore into buffer 0 (unsorted order is kept; a re-sort follows).
+int snapshot_restore(pic_t* h, Snapshot* sn) {
+  const size_t es = esize(h);
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaMemcpyAsync(h->fields, sn->fields, NCOMP * h->ncell * es, cudaMemcpyDeviceToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(h->curl, sn->curl, 3 * h->ncell * es, cudaMemcpyDeviceToDevice, h->stream));
+  const PartBuf& b = h->pb[0];
+  const char* src = (const char*)sn->part;
+  const size_t n = sn->np;
+  CK(h, cudaMemcpyAsync(b.cell, src, 4 * n, cudaMemcpyDeviceToDevice, h->stream));
+  src += 4 * n;
+  for (int d = 0; d < 3; ++d, src += es * n) CK(h, cudaMemcpyAsync(b.o[d], src, es * n, cudaMemcpyDeviceToDevice, h->stream));
+  for (int d = 0; d < 3; ++d, src += es * n) CK(h, cudaMemcpyAsync(b.u[d], src, es * n, cudaMemcpyDeviceToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(b.w, src, es * n, cudaMemcpyDeviceToDevice, h->stream));
+  src += es * n;
+  if (b.id) CK(h, cudaMemcpyAsync(b.id, src, 4 * n, cudaMemcpyDeviceToDevice, h->stream));
+  int ctrl[6];
+  std::memcpy(ctrl, sn->ctrl, sizeof(ctrl));
+  ctrl[0] = sn->np;
+  ctrl[1] = 0;
+  CK(h, cudaMemcpyAsync(h->d_ctrl, ctrl, sizeof(ctrl), cudaMemcpyHostToDevice, h->stream));
+  h->cur = 0;
+  h->step = sn->step;
+  h->shifts = sn->shifts;
+  h->origin = sn->origin;
+  h->win_frac = sn->win_frac;
+  h->curl_valid = sn->curl_valid;
+  h->need_sort = true;
+  CK(h, cudaStreamSynchronize(h->stream));
+  dfree(h, sn->fields);
+  dfree(h, sn->curl);
+  dfree(h, sn->part);
+  return PIC_OK;
+}
+
+std::string tune_key(const pic_t* h) {
+  char buf[128];
+  std::snprintf(buf, sizeof(buf), "%s:ppc%d:%dx%dx%d", h->precision == PIC_FP64 ? "fp64" : "fp32", h->ppc, h->nx,
+                h->ny, h->nz);
+  return buf;
+}
+
+// Tiny JSON cache {"key": [tx, ty, tz], ...}.
+bool cache_lookup(const char* path, const std::string& key, int t3[3]) {
+  if (!path) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  std::string txt;
+  char buf[4096];
+  size_t n;
+  while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, n);
+  std::fclose(f);
+  const std::string pat = "\"" + key + "\"";
+  size_t p = txt.find(pat);
+  if (p == std::string::npos) return false;
+  p = txt.find('[', p);
+  if (p == std::string::npos) return false;
+  return std::sscanf(txt.c_str() + p, "[%d, %d, %d]", &t3[0], &t3[1], &t3[2]) == 3;
+}
+
+void cache_store(const char* path, const std::string& key, const int t3[3]) {
+  if (!path) return;
+  std::string txt;
+  if (FILE* f = std::fopen(path, "r")) {
+    char buf[4096];
+    size_t n;
+    while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, n);
+    std::fclose(f);
+  }
+  std::vector<std::string> entries;
+  // keep the other entries (one per line between the braces)
+  size_t a = 0;
+  while ((a = txt.find('"', a)) != std::string::npos) {
+    size_t b = txt.find(']', a);
+    if (b == std::string::npos) break;
+    std::string e = txt.substr(a, b - a + 1);
+    if (e.find("\"" + key + "\"") != 0) entries.push_back(e);
+    a = b + 1;
+  }
+  char buf[160];
+  std::snprintf(buf, sizeof(buf), "\"%s\": [%d, %d, %d]", key.c_str(), t3[0], t3[1], t3[2]);
+  entries.push_back(buf);
+  FILE* f = std::fopen(path, "w");
+  if (!f) return;
+  std::fputs("{\n", f);
+  for (size_t i = 0; i < entries.size(); ++i) std::fprintf(f, "  %s%s\n", entries[i].c_str(), i + 1 < entries.size() ? "," : "");
+  std::fputs("}\n", f);
+  std::fclose(f);
+}
+
+template <typename T>
+int autotune_impl(pic_t* h, int steps, const char* cache_path, int out3[3], double* best_ms) {
+  const std::string key = tune_key(h);
+  int t3[3];
+  if (cache_lookup(cache_path, key, t3)) {
+    int rc = set_tiles(h, t3[0], t3[1], t3[2]);
+    if (rc) return rc;
+    for (int d = 0; d < 3; ++d) out3[d] = t3[d];
+    *best_ms = -1.0;
+    return PIC_OK;
+  }
+  static const int cand[][3] = {{8, 8, 8}, {16, 8, 8}, {8, 4, 4}, {16, 4, 4}, {32, 4, 4},
+                                {4, 8, 8}, {8, 8, 4}, {16, 8, 4}, {4, 4, 4}, {12, 6, 6}};
+  const Tiles orig = h->tiles;
+  double best = 1e300;
+  int bi = -1;
+  const bool prof = h->profiling;
+  for (int c = 0; c < (int)(sizeof(cand) / sizeof(cand[0])); ++c) {
+    Tiles trial = h->tiles;
+    (void)trial;
+    if (set_tiles(h, cand[c][0], cand[c][1], cand[c][2]) != PIC_OK) continue;
+    Snapshot sn;
+    int rc = snapshot_take(h, &sn);
+    if (rc) return rc;
+    rc = resort_all<T>(h);
+    if (rc) return rc;
+    h->need_sort = false;
+    rc = step_impl<T>(h, 1);  // warm-up
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    CK(h, cudaEventRecord(e0, h->stream));
+    rc = step_impl<T>(h, steps);
+    if (rc) return rc;
+    CK(h, cudaEventRecord(e1, h->stream));
+    CK(h, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    rc = snapshot_restore(h, &sn);
+    if (rc) return rc;
+    const double per = ms / std::max(steps, 1);
+    if (per < best) {
+      best = per;
+      bi = c;
+    }
+  }
+  h->profiling = prof;
+  int rc;
+  if (bi < 0)
+    rc = set_tiles(h, orig.tx, orig.ty, orig.tz);
+  else
+    rc = set_tiles(h, cand[bi][0], cand[bi][1], cand[bi][2]);
+  if (rc) return rc;
+  out3[0] = h->tiles.tx;
+  out3[1] = h->tiles.ty;
+  out3[2] = h->tiles.tz;
+  *best_ms = best;
+  cache_store(cache_path, key, out3);
+  return check_device_error(h);
+}
+
+}  // namespace
+
+extern "C" int pic_autotune(pic_t* h, int steps, const char* cache_path, int* tile_out, double* ms_out) {
+  if (!h || steps < 1) return PIC_ERR_ARG;
+  if (h->batched) return fail(h, PIC_ERR_STATE, "handle is part of a batch");
+  if (!h->tiled) return fail(h, PIC_ERR_STATE, "autotuning needs the tiled particle path");
+  if (!cache_path) cache_path = std::getenv("PIC_AUTOTUNE_CACHE");
+  int t3[3];
+  double ms = 0.0;
+  int rc = h->precision == PIC_FP64 ? autotune_impl<double>(h, steps, cache_path, t3, &ms)
+                                    : autotune_impl<float>(h, steps, cache_path, t3, &ms);
+  if (rc) return rc;
+  if (tile_out)
+    for (int d = 0; d < 3; ++d) tile_out[d] = t3[d];
+  if (ms_out) *ms_out = ms;
+  return PIC_OK;
+}
+
+extern "C" int pic_set_tiles(pic_t* h, int tx, int ty, int tz) {
+  if (!h || tx < 1 || ty < 1 || tz < 1) return PIC_ERR_ARG;
+  if (h->batched) return fail(h, PIC_ERR_STATE, "handle is part of a batch");
+  return set_tiles(h, tx, ty, tz);
+}
+
+// ===========================================================================
+// Batched instances: one CUDA graph launch per step for all members.
 // ===========================================================================
 struct pic_batch_t {
   std::vector<pic_t*> sims;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  std::vector<int> cur0;
+  int parity = 0;
+  bool stale = true;
+  long long kernels_per_step = 0;
+  long long graph_launches = 0, kernel_launches = 0;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  double last_ms = 0.0;
+  std::string err;
 };
+
+namespace {
+
+int bfail(pic_batch_t* b, int code, const std::string& m) {
+  b->err = m;
+  return code;
+}
+
+// One step of member h on stream s, every step parameter read from the
+// device-side state (so the same captured launches replay every step).
+int enqueue_step_dyn(pic_t* h, cudaStream_t s, int cur, long long* kernels) {
+  using T = float;
+  const size_t n = h->ncell;
+  const Tiles tl = h->tiles;
+  const int nb = 1 - cur;
+  Geom<T> g = geom<T>(h);
+  g.dyn = h->d_dyn;
+  Geom<T> gs = g;
+  gs.gate = 1;
+  Fields<T> f = fields<T>(h);
+  const FieldCoef<T> fc = field_coef<T>(h);
+  const Smooth<T> S = smooth<T>(h);
+  CK(h, cudaMemsetAsync(f.c[JX], 0, 3 * n * sizeof(T), s));
+  CK(h, cudaMemsetAsync(h->tcnt, 0, sizeof(int) * tl.n, s));
+  k_step_begin<<<1, 32, 0, s>>>(h->d_dyn);
+  const T hq = (T)(h->q * h->dt / (2.0 * h->m));
+  k_push_tiled<T><<<tl.n, 256, tiled_smem_bytes<T>(tl), s>>>(g, tl, f, parts<T>(h, cur), h->tstart[cur],
+                                                            (int)h->capacity, h->keys, h->tcnt, hq, (T)h->q, 0,
+                                                            x_lo(h), x_hi(h), h->d_pushed, h->d_ctrl + 2);
+  k_e_update<T><<<grid_for(n), 256, 0, s>>>(g, f, curl_view<T>(h), fc);
+  k_curl_update<T><<<grid_for(n), 256, 0, s>>>(g, S, f, curl_view<T>(h), fc, 1, 0, h->nx);
+  k_window_commit<<<1, 32, 0, s>>>(h->d_dyn);
+  k_zero_front_slab<T><<<grid_for((long long)NCOMP * h->ny * h->nz), 256, 0, s>>>(gs, f);
+  k_curl_update<T><<<grid_for((long long)h->ny * h->nz), 256, 0, s>>>(gs, S, f, curl_view<T>(h), fc, 0, 0, 1);
+  k_curl_update<T><<<grid_for((long long)h->ny * h->nz), 256, 0, s>>>(gs, S, f, curl_view<T>(h), fc, 0, h->nx - 1, 1);
+  LoadSpec L;
+  const bool inject = h->has_species;
+  const long long nslot = (long long)h->ny * h->nz * std::max(h->ppc, 1);
+  if (inject) {
+    L = load_spec(h, x_hi(h), x_hi(h));
+    k_inject_tiled<T><<<grid_for(nslot, 256, 152 * 16), 256, 0, s>>>(gs, tl, parts<T>(h, nb), L, 0, h->tcnt,
+                                                                     h->tstart[nb], h->tfill, h->d_ctrl + 2);
+  }
+  k_scan_tiles<<<1, 1024, 0, s>>>(h->tcnt, h->tstart[nb], tl.n, h->d_ctrl + nb, (int)h->capacity, h->d_ctrl + 2);
+  CK(h, cudaMemsetAsync(h->tfill, 0, sizeof(int) * tl.n, s));
+  k_scatter<T><<<grid_for(h->capacity, 256, 152 * 16), 256, 0, s>>>(parts<T>(h, cur), h->keys, h->d_ctrl + cur,
+                                                                     parts<T>(h, nb), h->tstart[nb], h->tfill,
+                                                                     h->d_ctrl + 2);
+  if (inject)
+    k_inject_tiled<T><<<grid_for(nslot, 256, 152 * 16), 256, 0, s>>>(gs, tl, parts<T>(h, nb), L, 1, h->tcnt,
+                                                                     h->tstart[nb], h->tfill, h->d_ctrl + 2);
+  *kernels += 11 + (inject ? 2 : 0);
+  CK(h, cudaGetLastError());
+  return PIC_OK;
+}
+
+int dyn_to_device(pic_t* h) {
+  DynState d;
+  d.frac = h->win_frac;
+  d.frac_new = h->win_frac;
+  d.v = h->win_v;
+  d.dt = h->dt;
+  d.dx = h->dx;
+  d.t0 = h->win_t0;
+  d.step = h->step;
+  d.shifts = h->shifts;
+  d.origin = h->origin;
+  d.origin_after = h->origin;
+  d.shift = 0;
+  d.has_window = h->has_window ? 1 : 0;
+  d.nx = h->nx;
+  CK(h, cudaMemcpyAsync(h->d_dyn, &d, sizeof(d), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+int dyn_to_host(pic_t* h) {
+  DynState d;
+  CK(h, cudaMemcpy(&d, h->d_dyn, sizeof(d), cudaMemcpyDeviceToHost));
+  h->win_frac = d.frac;
+  h->step = d.step;
+  h->shifts = d.shifts;
+  h->origin = d.origin;
+  return PIC_OK;
+}
+
+void drop_graphs(pic_batch_t* b) {
+  for (int p = 0; p < 2; ++p)
+    if (b->exec[p]) {
+      cudaGraphExecDestroy(b->exec[p]);
+      b->exec[p] = nullptr;
+    }
+  b->stale = true;
+}
+
+// Bring every member to a capturable state and capture the two step graphs
+// (members alternate their particle buffers, so even and odd steps differ).
+int prepare_and_capture(pic_batch_t* b) {
+  drop_graphs(b);
+  b->cur0.assign(b->sims.size(), 0);
+  for (size_t i = 0; i < b->sims.size(); ++i) {
+    pic_t* h = b->sims[i];
+    if (h->need_sort) {
+      int rc = resort_all<float>(h);
+      if (rc) return bfail(b, rc, h->err);
+      h->need_sort = false;
+    }
+    if (!h->curl_valid) {
+      int rc = curl_only<float>(h, 0, h->nx);
+      if (rc) return bfail(b, rc, h->err);
+      h->curl_valid = true;
+    }
+    int rc = dyn_to_device(h);
+    if (rc) return bfail(b, rc, h->err);
+    b->cur0[i] = h->cur;
+  }
+  for (int p = 0; p < 2; ++p) {
+    long long kernels = 0;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return bfail(b, PIC_ERR_CUDA, "cudaStreamBeginCapture failed");
+    cudaEventRecord(b->fork, b->stream);
+    int rc = PIC_OK;
+    for (size_t i = 0; i < b->sims.size() && rc == PIC_OK; ++i) {
+      cudaStreamWaitEvent(b->side[i], b->fork, 0);
+      rc = enqueue_step_dyn(b->sims[i], b->side[i], b->cur0[i] ^ p, &kernels);
+      cudaEventRecord(b->join[i], b->side[i]);
+      cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return bfail(b, rc, "capture of a member step failed");
+    }
+    if (e != cudaSuccess || !graph) return bfail(b, PIC_ERR_CUDA, "cudaStreamEndCapture failed");
+    e = cudaGraphInstantiate(&b->exec[p], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(b, PIC_ERR_CUDA, "cudaGraphInstantiate failed");
+    b->kernels_per_step = kernels;
+  }
+  b->parity = 0;
+  b->stale = false;
+  return PIC_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1151,13 +1581,32 @@ int pic_batch_create(int n, pic_t* const* sims, pic_batch_t** out) {
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!sims[i]) return PIC_ERR_ARG;
-    if (sims[i]->precision != PIC_FP32 || sims[i]->batched) return PIC_ERR_STATE;
+    if (sims[i]->precision != PIC_FP32 || sims[i]->batched || !sims[i]->tiled) return PIC_ERR_STATE;
+    if (sims[i]->laser_mode == PIC_LASER_HARD_SOURCE) return PIC_ERR_STATE;  // time-driven source: host path only
     for (int j = 0; j < i; ++j)
       if (sims[j] == sims[i]) return PIC_ERR_ARG;
   }
   pic_batch_t* b = new (std::nothrow) pic_batch_t();
   if (!b) return PIC_ERR_OOM;
   b->sims.assign(sims, sims + n);
+  bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreate(&b->t0) == cudaSuccess && cudaEventCreate(&b->t1) == cudaSuccess;
+  b->side.assign(n, nullptr);
+  b->join.assign(n, nullptr);
+  for (int i = 0; i < n && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < n && ok; ++i) {
+    pic_t* h = sims[i];
+    if (!h->d_dyn) h->d_dyn = (DynState*)dalloc(h, sizeof(DynState));
+    ok = h->d_dyn != nullptr && cudaStreamSynchronize(h->stream) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    pic_batch_destroy(b);
+    return PIC_ERR_CUDA;
+  }
   for (pic_t* s : b->sims) s->batched = true;
   *out = b;
   return PIC_OK;
@@ -1165,15 +1614,44 @@ int pic_batch_create(int n, pic_t* const* sims, pic_batch_t** out) {
 
 int pic_batch_step(pic_batch_t* b, int n) {
   if (!b || n < 0) return PIC_ERR_ARG;
-  for (int it = 0; it < n; ++it)
-    for (pic_t* s : b->sims) {
-      int rc = step_impl<float>(s, 1);
-      if (rc) return rc;
-    }
+  if (n == 0) return PIC_OK;
   for (pic_t* s : b->sims) {
-    int rc = check_device_error(s);
+    int rc = grow_if_needed(s);
+    if (rc) return bfail(b, rc, s->err);
+    if (s->need_sort) b->stale = true;
+  }
+  if (b->stale) {
+    int rc = prepare_and_capture(b);
     if (rc) return rc;
   }
+  cudaEventRecord(b->t0, b->stream);
+  for (int it = 0; it < n; ++it) {
+    if (cudaGraphLaunch(b->exec[b->parity], b->stream) != cudaSuccess)
+      return bfail(b, PIC_ERR_CUDA, "cudaGraphLaunch failed");
+    b->parity ^= 1;
+    b->graph_launches += 1;
+    b->kernel_launches += b->kernels_per_step;
+  }
+  cudaEventRecord(b->t1, b->stream);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, PIC_ERR_CUDA, "batch step failed");
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, b->t0, b->t1) == cudaSuccess) b->last_ms = ms;
+  for (size_t i = 0; i < b->sims.size(); ++i) {
+    pic_t* h = b->sims[i];
+    h->cur = b->cur0[i] ^ b->parity;
+    int rc = dyn_to_host(h);
+    if (!rc) rc = check_device_error(h);
+    if (rc) return bfail(b, rc, h->err);
+  }
+  return PIC_OK;
+}
+
+int pic_batch_info(const pic_batch_t* b, int64_t* graph_launches, int64_t* kernel_launches,
+                   double* last_step_ms) {
+  if (!b) return PIC_ERR_ARG;
+  if (graph_launches) *graph_launches = b->graph_launches;
+  if (kernel_launches) *kernel_launches = b->kernel_launches;
+  if (last_step_ms) *last_step_ms = b->last_ms;
   return PIC_OK;
 }
 
@@ -1184,7 +1662,17 @@ int pic_batch_diag(pic_batch_t* b, int instance, int kind, double* out, size_t l
 
 int pic_batch_destroy(pic_batch_t* b) {
   if (!b) return PIC_ERR_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graphs(b);
   for (pic_t* s : b->sims) s->batched = false;
+  for (cudaStream_t s : b->side)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->t0) cudaEventDestroy(b->t0);
+  if (b->t1) cudaEventDestroy(b->t1);
+  if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return PIC_OK;
 }

@@ -13,6 +13,21 @@ enum { EX = 0, EY, EZ, BX, BY, BZ, JX, JY, JZ, NCOMP };
 // Grid geometry as the kernels see it.  Field arrays are [slab][j][k] with
 // the x slab stored in a ring: window-relative slab i lives at storage slab
 // (i + origin) mod nx, so the moving window never copies a field.
+// Per-instance step state kept on the device, so that a captured CUDA graph
+// can replay steps: the FP64 window accumulator, the ring origin and the
+// shift decision of the current step.
+struct DynState {
+  double frac;      // window accumulator, cells
+  double frac_new;  // accumulator at the end of the current step
+  double v, dt, dx, t0;  // window speed (c), time step, cell, start time
+  long long step, shifts;
+  int origin;        // storage slab of window-relative slab 0
+  int origin_after;  // origin once the current step's shift is applied
+  int shift;         // 1 if the current step ends with a window shift
+  int has_window;
+  int nx;
+};
+
 template <typename T>
 struct Geom {
   int nx, ny, nz;
@@ -20,7 +35,19 @@ struct Geom {
   int periodic_x;  // 1: x periodic; 0: open (zero outside the window)
   int nyz;         // ny * nz
   T dt, dx, dy, dz;
+  const DynState* dyn;  // non-null: origin (and shift) come from the device
+  int gate;             // with dyn: 1 = the kernel runs only on a shift step
 };
+
+// Apply the device-side step state to a kernel's geometry; false means the
+// kernel has nothing to do this step.
+template <typename T>
+__device__ __forceinline__ bool dyn_prologue(Geom<T>& g) {
+  if (!g.dyn) return true;
+  if (g.gate && !g.dyn->shift) return false;
+  g.origin = g.dyn->origin;
+  return true;
+}
 
 // Smoothing stencils S_x, S_y, S_z of Sec. 2 (centre, first-transverse edge,
 // second-transverse edge, corner); transverse order (y,z), (x,z), (x,y).

@@ -145,6 +145,7 @@ __device__ __forceinline__ T bhalf(const T* __restrict__ B, const T* __restrict_
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_e_update(Geom<T> g, Fields<T> f, Fields<T> cc, FieldCoef<T> fc) {
+  if (!dyn_prologue(g)) return;
   const int nyz = g.nyz;
   const long long ncell = (long long)g.nx * nyz;
   const T *Bx = f.c[BX], *By = f.c[BY], *Bz = f.c[BZ];
@@ -187,6 +188,7 @@ __device__ __forceinline__ void curl_smoothed(const Geom<T>& g, const Smooth<T>&
 template <typename T>
 __global__ void __launch_bounds__(256) k_curl_update(Geom<T> g, Smooth<T> S, Fields<T> f, Fields<T> cc,
                                                     FieldCoef<T> fc, int mode, int i0, int ni) {
+  if (!dyn_prologue(g)) return;
   const int nyz = g.nyz;
   const long long ncell = (long long)ni * nyz;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
@@ -631,6 +633,51 @@ __global__ void __launch_bounds__(256) k_particle_diag(Parts<T> p, const int* __
   if (kind == 0) {
     acc = block_sum(acc);
     if (threadIdx.x == 0) atomicAdd(out, acc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Device-side step state (graph-replayed batch steps).
+// ---------------------------------------------------------------------------
+// Start of a step: decide whether it ends with a window shift (the same FP64
+// accumulator arithmetic as the host path, without contraction).
+static __global__ void k_step_begin(DynState* d) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double t_old = __dmul_rn((double)d->step, d->dt);
+  const double t_new = __dmul_rn((double)(d->step + 1), d->dt);
+  double fn = d->frac;
+  if (d->has_window && t_new > d->t0) {
+    const double span = t_old >= d->t0 ? d->dt : __dsub_rn(t_new, d->t0);
+    fn = __dadd_rn(d->frac, __ddiv_rn(__dmul_rn(d->v, span), d->dx));
+  }
+  d->frac_new = fn;
+  d->shift = fn >= 1.0 ? 1 : 0;
+  d->origin_after = d->shift ? (d->origin + 1) % d->nx : d->origin;
+}
+
+// After the field update: commit the step and the shift.
+static __global__ void k_window_commit(DynState* d) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  d->step += 1;
+  if (d->shift) {
+    d->frac = __dsub_rn(d->frac_new, 1.0);
+    d->origin = d->origin_after;
+    d->shifts += 1;
+  } else {
+    d->frac = d->frac_new;
+  }
+}
+
+// On a shift step: zero all components of the storage slab that left the
+// window at the back (it is the new front slab).
+template <typename T>
+__global__ void k_zero_front_slab(Geom<T> g, Fields<T> f) {
+  if (!dyn_prologue(g)) return;
+  const int slab = (g.origin + g.nx - 1) % g.nx;
+  const long long n = (long long)NCOMP * g.nyz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(q / g.nyz), r = (int)(q - (long long)c * g.nyz);
+    f.c[c][(size_t)slab * g.nyz + r] = T(0);
   }
 }
 

@@ -111,6 +111,8 @@ int diag_noalloc(pic_t* h, int kind, double* out, size_t len, const pic_diag_arg
   g.dx = (T)h->dx;
   g.dy = (T)h->dy;
   g.dz = (T)h->dz;
+  g.dyn = nullptr;
+  g.gate = 0;
   Fields<T> f;
   for (int c = 0; c < NCOMP; ++c) f.c[c] = (T*)h->fields + (size_t)c * h->ncell;
   Parts<T> p;

@@ -49,6 +49,8 @@ struct pic_t {
   int* tcnt = nullptr;      // per-tile counts of the next buffer
   int* tfill = nullptr;     // per-tile fill counters of the scatter
   bool need_sort = false;   // particles not grouped by tile (after load/set)
+  int tiles_alloc = 0;      // tile entries the tile arrays were sized for
+  pic::DynState* d_dyn = nullptr;  // device-side step state (batched stepping)
   pic::PartBuf pb[2];       // current and compaction target
   int cur = 0;
   long long capacity = 0;

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_push_tiled(Geom
                                                    unsigned long long* pushed, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
+  if (g.dyn) origin_after = g.dyn->origin_after;
   const int t = blockIdx.x;
   const int pbeg = min(tstart[t], capacity), pend = min(tstart[t + 1], capacity);
   if (pbeg >= pend) return;
@@ -382,6 +383,8 @@ __global__ void k_scatter(Parts<T> src, const int* __restrict__ keys, const int*
 template <typename T>
 __global__ void k_inject_tiled(Geom<T> g, Tiles tl, Parts<T> p, LoadSpec L, int pass, int* cnt,
                                const int* __restrict__ tstart, int* fill, int* err) {
+  if (!dyn_prologue(g)) return;
+  if (g.dyn) L.shifts = g.dyn->shifts;
   const long long nslot = (long long)(L.hi - L.lo + 1) * g.nyz * L.ppc;
   for (long long q0 = (long long)blockIdx.x * blockDim.x; q0 < nslot; q0 += (long long)gridDim.x * blockDim.x) {
     const long long qq = q0 + threadIdx.x;

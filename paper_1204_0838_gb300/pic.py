@@ -105,6 +105,11 @@ _SIGS = {
     "pic_batch_diag": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double),
                                  C.c_size_t, C.POINTER(pic_diag_args)]),
     "pic_batch_destroy": (C.c_int, [C.c_void_p]),
+    "pic_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_double)]),
+    "pic_set_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "pic_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_char_p, C.POINTER(C.c_int),
+                               C.POINTER(C.c_double)]),
 }
 
 
@@ -318,6 +323,24 @@ def pic_batch_diag(b, instance, kind, length=1, gamma_min=0.0, e_min=0.0, e_max=
     _check(lib().pic_batch_diag(b, int(instance), int(kind), _dp(out), out.size, C.byref(a)),
            "pic_batch_diag")
     return out
+
+
+def pic_batch_info(b):
+    g, k, ms = C.c_int64(), C.c_int64(), C.c_double()
+    _check(lib().pic_batch_info(b, C.byref(g), C.byref(k), C.byref(ms)), "pic_batch_info")
+    return {"graph_launches": g.value, "kernel_launches": k.value, "last_step_ms": ms.value}
+
+
+def pic_set_tiles(h, tx, ty, tz):
+    _check(lib().pic_set_tiles(h, int(tx), int(ty), int(tz)), "pic_set_tiles", h)
+
+
+def pic_autotune(h, steps=2, cache_path=None):
+    t = (C.c_int * 3)()
+    ms = C.c_double()
+    cp = cache_path.encode() if cache_path else None
+    _check(lib().pic_autotune(h, int(steps), cp, t, C.byref(ms)), "pic_autotune", h)
+    return (t[0], t[1], t[2]), ms.value
 
 
 def pic_batch_destroy(b):

@@ -218,18 +218,33 @@ def test_fp32_against_fp64_diagnostics():
 
 def test_batched_equals_single_fp32():
     cfg = _window_cfg()
-    singles = [make_gpu(dict(cfg, seed=cfg["seed"] + i, a0=2 + i), precision="fp32") for i in range(3)]
-    batch_members = [make_gpu(dict(cfg, seed=cfg["seed"] + i, a0=2 + i), precision="fp32") for i in range(3)]
+    sizes = [(96, 24, 24), (64, 16, 32), (80, 24, 16)]  # uneven instances
+    cfgs = []
+    for i, crop in enumerate(sizes):
+        c = dict(cfg, seed=cfg["seed"] + i, a0=2 + i)
+        c["nx"], c["ny"], c["nz"] = crop
+        c["x0"] = -(crop[0] // 2) * c["dx"]
+        cfgs.append(c)
+    singles = [make_gpu(c, precision="fp32") for c in cfgs]
+    batch_members = [make_gpu(c, precision="fp32") for c in cfgs]
+    pic.pic_set_tiles(batch_members[1].h, 16, 4, 8)  # members may differ in tiling
     b = pic.pic_batch_create([m.h for m in batch_members])
     try:
-        pic.pic_batch_step(b, 20)
+        pic.pic_batch_step(b, 7)   # odd count: the two captured graphs alternate
+        pic.pic_batch_step(b, 13)
+        info = pic.pic_batch_info(b)
+        assert info["graph_launches"] == 20
         for s in singles:
             s.step(20)
         for i, s in enumerate(singles):
+            assert batch_members[i].info()["step"] == 20
+            assert batch_members[i].info()["shifts"] == s.info()["shifts"] == 20
+            assert batch_members[i].info()["np"] == s.info()["np"]
+        for i, s in enumerate(singles):
             e_b = pic.pic_batch_diag(b, i, pic.PIC_DIAG_FIELD_ENERGY)[0]
             assert abs(e_b / s.diag("field_energy")[0] - 1) < 1e-4
-            lb = pic.pic_batch_diag(b, i, pic.PIC_DIAG_EX_LINEOUT, cfg["nx"])
-            ls = s.diag("ex_lineout", cfg["nx"])
+            lb = pic.pic_batch_diag(b, i, pic.PIC_DIAG_EX_LINEOUT, cfgs[i]["nx"])
+            ls = s.diag("ex_lineout", cfgs[i]["nx"])
             assert np.linalg.norm(lb - ls) <= 1e-4 * np.linalg.norm(ls)
         with pytest.raises(pic.PicError):
             batch_members[0].step(1)  # members are stepped by their batch only
@@ -256,3 +271,27 @@ def test_error_codes():
     with pytest.raises(pic.PicError) as e:
         g.set_particles(np.array([[0.5], [1.0], [1.0]]), np.zeros((3, 1)), np.ones(1))
     assert e.value.code == -1  # x cell 0 is outside the open-x allowed range
+
+
+def test_autotune_restores_state_and_keeps_results(tmp_path):
+    shape = (40, 16, 16)
+    g, o = _pair(shape, False)
+    _set_random(g, o, shape, 12000, seed=8, periodic=False)
+    f0 = g.fields()
+    p0 = by_id(g.particles())
+    cache = str(tmp_path / "tiles.json")
+    tile, ms = pic.pic_autotune(g.h, 1, cache)
+    assert ms > 0 and all(t >= 1 for t in tile)
+    assert g.info()["step"] == 0
+    assert np.array_equal(g.fields(), f0)
+    p1 = by_id(g.particles())
+    assert np.array_equal(p1["xi"], p0["xi"]) and np.array_equal(p1["u"], p0["u"])
+    # the cached choice is reused without trials
+    g2, _ = _pair(shape, False)
+    _set_random(g2, o, shape, 12000, seed=8, periodic=False)
+    tile2, ms2 = pic.pic_autotune(g2.h, 1, cache)
+    assert tile2 == tile and ms2 < 0
+    g.step(2)
+    o.step(2)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
