@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--start-step", type=int, default=-1)
     ap.add_argument("--crop", default="", help="nx,ny,nz (profiling small cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default 8x8x8 tiles")
     return ap.parse_args()
 
 
@@ -225,6 +226,10 @@ def run_ours(args):
                 window=cfg["window"])
     g.add_species(cfg["prof_x"], cfg["prof_n"], cfg["ppc"], loading=cfg["loading"])
     g.add_laser(cfg["a0"], cfg["waist"], cfg["fwhm"], cfg["lambda0"], cfg["x_focus"], cfg["t_peak"])
+    tile = (8, 8, 8)
+    if not args.no_autotune:
+        cache = os.environ.get("PIC_AUTOTUNE_CACHE", "/tmp/pic_autotune_%d.json" % os.getpid())
+        tile, _ = pic.pic_autotune(g.h, 1, cache)
     for _ in range(args.warmup):
         g.step(1)
     torch.cuda.synchronize()
@@ -302,7 +307,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32",
-            "data": "synthetic", "config": _describe(cfg, start, precision),
+            "data": "synthetic", "config": dict(_describe(cfg, start, precision), tile=list(tile)),
             "particles": info["np"], "roofline": roofline, "clocks": clk,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32,
                     "note": "pic_step(1) + pic_diag(field energy) into a host buffer per step; "

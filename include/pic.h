@@ -60,6 +60,8 @@ extern "C" {
 #define PIC_BC_OPEN 1 /* x only: fields zero outside the window, particles absorbed */
 #define PIC_LOAD_RANDOM 0  /* ppc independent uniform positions per cell      */
 #define PIC_LOAD_LATTICE 1 /* jittered sub-lattice: ppc 1,2,4,8 = 1x1x1,1x2x1,1x2x2,2x2x2 */
+#define PIC_SOLVER_PERFECT 0 /* Sec. 2 smoothed curl, c dt = dx by default         */
+#define PIC_SOLVER_YEE 1     /* standard Yee curl (S_i = 1), Courant-limited dt  */
 #define PIC_LASER_AUTO 0
 #define PIC_LASER_HARD_SOURCE 1 /* Ey imposed on the i = 0 plane each step   */
 #define PIC_LASER_IN_BOX 2      /* paraxial pulse initialised inside the box  */
@@ -88,6 +90,9 @@ typedef struct pic_grid {
                            currents; the window accumulator and diagnostic
                            reductions stay FP64)                              */
   int bc_x;             /* PIC_BC_PERIODIC or PIC_BC_OPEN                      */
+  int solver;           /* PIC_SOLVER_PERFECT (the paper's method) or
+                           PIC_SOLVER_YEE (normal dispersion, for comparison;
+                           Sec. 1 and Sec. 3.3 contrast the two)              */
   uint64_t seed;        /* particle-loading seed (SplitMix64 counter keys)     */
   uint32_t flags;       /* PIC_FLAG_*                                          */
   int64_t max_particles;/* particle capacity; <= 0 selects ppc * cells         */
@@ -152,9 +157,11 @@ typedef struct pic_batch_t pic_batch_t;
 const char* pic_last_error(const pic_t* h);
 const char* pic_version(void);
 
-/* Create a simulation (Sec. 2, Sec. 3.1).  dt <= 0 selects c dt = dx (the
- * perfect-dispersion time step tied to the coarse longitudinal cell); an
- * explicit dt must satisfy 0 < c dt <= dx.  w == NULL: no moving window.
+/* Create a simulation (Sec. 2, Sec. 3.1).  With the perfect-dispersion solver
+ * dt <= 0 selects c dt = dx (the time step tied to the coarse longitudinal
+ * cell) and an explicit dt must satisfy 0 < c dt <= dx.  With the Yee solver
+ * dt <= 0 selects 0.999 of the Courant limit 1 / (c sqrt(dx^-2 + dy^-2 +
+ * dz^-2)) and an explicit dt must not exceed that limit.  w == NULL: no moving window.
  * A window requires bc_x == PIC_BC_OPEN.  Errors: PIC_ERR_ARG (dx > dy or
  * dx > dz, bad sizes, nx < 16 or ny, nz < 4), PIC_ERR_OOM, PIC_ERR_CUDA. */
 int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out);

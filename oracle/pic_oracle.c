@@ -49,7 +49,7 @@
 #define OC_PI 3.14159265358979323846
 
 struct or_sim {
-  int nx, ny, nz, periodic_x;
+  int nx, ny, nz, periodic_x, solver;
   double dx, dy, dz, dt; /* normalised */
   double lambda0, omega0, k0; /* SI: m, 1/s, 1/m */
   double x0;                  /* normalised lab x of node 0 at t = 0 */
@@ -120,6 +120,14 @@ static double uniform01(uint64_t seed, uint64_t n) {
 /* ------------------------------------------------------------------ */
 static void smoothing_coefficients(or_sim* s) {
   double r[3];
+  if (s->solver == 1) { /* standard Yee curl: no smoothing */
+    for (int a = 0; a < 3; ++a) {
+      s->alpha[a] = 1.0;
+      s->gam[a] = 0.0;
+      for (int b = 0; b < 3; ++b) s->beta[a][b] = 0.0;
+    }
+    return;
+  }
   r[0] = 1.0;
   r[1] = (s->dx / s->dy) * (s->dx / s->dy);
   r[2] = (s->dx / s->dz) * (s->dx / s->dz);
@@ -613,10 +621,24 @@ or_sim* or_create(const or_grid* g, double dt_si, const or_window* w) {
   s->dz = g->dz * s->k0;
   s->x0 = g->x0 * s->k0;
   s->seed = g->seed;
-  s->dt = dt_si > 0 ? dt_si * s->omega0 : s->dx;
-  if (s->dt > s->dx * (1.0 + 1e-12)) {
+  if (g->solver != 0 && g->solver != 1) {
     free(s);
     return NULL;
+  }
+  s->solver = g->solver;
+  if (s->solver == 1) { /* Yee: Courant limit 1 / sqrt(sum 1/d^2) */
+    double lim = 1.0 / sqrt(1.0 / (s->dx * s->dx) + 1.0 / (s->dy * s->dy) + 1.0 / (s->dz * s->dz));
+    s->dt = dt_si > 0 ? dt_si * s->omega0 : 0.999 * lim;
+    if (s->dt > lim * (1.0 + 1e-12)) {
+      free(s);
+      return NULL;
+    }
+  } else {
+    s->dt = dt_si > 0 ? dt_si * s->omega0 : s->dx;
+    if (s->dt > s->dx * (1.0 + 1e-12)) {
+      free(s);
+      return NULL;
+    }
   }
   smoothing_coefficients(s);
   size_t n = (size_t)s->nx * s->ny * s->nz;

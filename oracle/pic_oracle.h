@@ -44,6 +44,7 @@ typedef struct {
   double x0;                /* metres; lab x of node 0 at t = 0             */
   int periodic_x;           /* 1: periodic x, 0: open x (y, z periodic)     */
   uint64_t seed;            /* particle-loading seed                        */
+  int solver;               /* 0: perfect dispersion (Sec. 2), 1: Yee      */
 } or_grid;
 
 typedef struct {

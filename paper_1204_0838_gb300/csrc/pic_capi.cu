@@ -170,6 +170,13 @@ size_t esize(const pic_t* h) { return h->precision == PIC_FP64 ? 8 : 4; }
 // alpha + 2 beta + 2 beta + 4 gamma = 1; the dispersion function is then
 // 1 - (1 - s_x^2)(1 - r_y s_y^2)(1 - r_z s_z^2).
 void set_coefficients(pic_t* h) {
+  if (h->solver == PIC_SOLVER_YEE) {  // standard curl: every S_i is the identity
+    for (int a = 0; a < 3; ++a) {
+      h->sm_a[a] = 1.0;
+      h->sm_b1[a] = h->sm_b2[a] = h->sm_g[a] = 0.0;
+    }
+    return;
+  }
   const double r[3] = {1.0, (h->dx / h->dy) * (h->dx / h->dy), (h->dx / h->dz) * (h->dx / h->dz)};
   const int t1[3] = {1, 0, 0}, t2[3] = {2, 2, 1};
   for (int a = 0; a < 3; ++a) {
@@ -695,6 +702,7 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
   if (g->dx > g->dy || g->dx > g->dz) return PIC_ERR_ARG;  // Sec. 2: dx <= dy, dz
   if (g->precision != PIC_FP64 && g->precision != PIC_FP32) return PIC_ERR_ARG;
   if (g->bc_x != PIC_BC_PERIODIC && g->bc_x != PIC_BC_OPEN) return PIC_ERR_ARG;
+  if (g->solver != PIC_SOLVER_PERFECT && g->solver != PIC_SOLVER_YEE) return PIC_ERR_ARG;
   if (w && g->bc_x != PIC_BC_OPEN) return PIC_ERR_ARG;
   if (g->alloc && (!g->alloc->alloc || !g->alloc->free)) return PIC_ERR_ARG;
   pic_t* h = new (std::nothrow) pic_t();
@@ -715,10 +723,20 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
   h->seed = g->seed;
   h->flags = g->flags;
   h->max_particles = g->max_particles;
-  h->dt = dt > 0 ? dt * h->omega0 : h->dx;
-  if (h->dt > h->dx * (1.0 + 1e-12)) {
-    delete h;
-    return PIC_ERR_ARG;  // c dt <= dx keeps the scheme stable for dx <= dy, dz
+  h->solver = g->solver;
+  if (h->solver == PIC_SOLVER_YEE) {
+    const double lim = 1.0 / std::sqrt(1.0 / (h->dx * h->dx) + 1.0 / (h->dy * h->dy) + 1.0 / (h->dz * h->dz));
+    h->dt = dt > 0 ? dt * h->omega0 : 0.999 * lim;
+    if (h->dt > lim * (1.0 + 1e-12)) {
+      delete h;
+      return PIC_ERR_ARG;  // Courant limit of the standard Yee scheme
+    }
+  } else {
+    h->dt = dt > 0 ? dt * h->omega0 : h->dx;
+    if (h->dt > h->dx * (1.0 + 1e-12)) {
+      delete h;
+      return PIC_ERR_ARG;  // c dt <= dx keeps the scheme stable for dx <= dy, dz
+    }
   }
   if (g->alloc) {
     h->alloc = *g->alloc;

@@ -29,6 +29,7 @@ struct pic_t {
   int nx = 0, ny = 0, nz = 0;
   size_t ncell = 0;
   bool periodic_x = true;
+  int solver = PIC_SOLVER_PERFECT;
   double dx = 0, dy = 0, dz = 0, dt = 0;
   double lambda0 = 0, k0 = 0, omega0 = 0, x0 = 0;
   uint64_t seed = 0;

@@ -74,7 +74,7 @@ __device__ __forceinline__ T gather_smem(const T* __restrict__ s, int SY, int SZ
 // -1 when it leaves the open-x range once the window has moved to
 // origin_after); cnt_next[tile] counts the particles each tile will hold.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_push_tiled(Geom<T> g, Tiles tl, Fields<T> f, Parts<T> p,
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom<T> g, Tiles tl, Fields<T> f, Parts<T> p,
                                                    const int* __restrict__ tstart, int capacity,
                                                    int* __restrict__ keys, int* __restrict__ cnt_next,
                                                    T h, T q, int origin_after, int xlo, int xhi,

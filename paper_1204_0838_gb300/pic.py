@@ -18,6 +18,7 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_OOM", -4: "PIC_ERR
           -5: "PIC_ERR_TIMEOUT", -6: "PIC_ERR_NUMERIC", -7: "PIC_ERR_STATE"}
 PIC_FP64, PIC_FP32 = 0, 1
 PIC_BC_PERIODIC, PIC_BC_OPEN = 0, 1
+PIC_SOLVER_PERFECT, PIC_SOLVER_YEE = 0, 1
 PIC_LOAD_RANDOM, PIC_LOAD_LATTICE = 0, 1
 PIC_LASER_AUTO, PIC_LASER_HARD_SOURCE, PIC_LASER_IN_BOX = 0, 1, 2
 PIC_DIAG_EX_LINEOUT, PIC_DIAG_FIELD_ENERGY, PIC_DIAG_CHARGE, PIC_DIAG_SPECTRUM = 0, 1, 2, 3
@@ -36,7 +37,8 @@ class pic_grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
                 ("lambda0", C.c_double), ("x0", C.c_double),
-                ("precision", C.c_int), ("bc_x", C.c_int), ("seed", C.c_uint64),
+                ("precision", C.c_int), ("bc_x", C.c_int), ("solver", C.c_int),
+                ("seed", C.c_uint64),
                 ("flags", C.c_uint32), ("max_particles", C.c_int64),
                 ("alloc", C.POINTER(pic_alloc))]
 
@@ -356,11 +358,12 @@ class Sim:
 
     def __init__(self, nx, ny, nz, dx, dy, dz, lambda0, x0=0.0, periodic_x=True,
                  precision="fp64", seed=12040838, dt=0.0, window=None, track_ids=False,
-                 max_particles=0, use_torch=True):
+                 max_particles=0, use_torch=True, solver="perfect"):
         self._mem = TorchMemory() if use_torch else None
         g = pic_grid(nx, ny, nz, dx, dy, dz, lambda0, x0,
                      PIC_FP64 if precision == "fp64" else PIC_FP32,
-                     PIC_BC_PERIODIC if periodic_x else PIC_BC_OPEN, seed,
+                     PIC_BC_PERIODIC if periodic_x else PIC_BC_OPEN,
+                     PIC_SOLVER_YEE if solver == "yee" else PIC_SOLVER_PERFECT, seed,
                      PIC_FLAG_TRACK_IDS if track_ids else 0, int(max_particles),
                      C.pointer(self._mem.struct) if self._mem else None)
         w = pic_window(window[0], window[1]) if window is not None else None

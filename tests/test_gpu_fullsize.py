@@ -1,0 +1,119 @@
+"""Full-size parity: the c1 workload (1536x256x256 cells, ~1.2e8 particles) in
+the launch configuration bench.py times (autotuned tiles), checked against the
+FP64 oracle on sampled outputs.
+
+For a sampled node n the outcome of one step there depends only on a small
+neighbourhood: the particles whose start cell lies within [n-4, n+3] on every
+axis (the only ones whose Esirkepov window reaches nodes n-1 .. n+1) and the
+fields within a few cells.  The test copies a 16^3 block of the GPU's fields
+around n and those particles into a periodic 16^3 oracle box, steps it once,
+and compares with the GPU's full-size step: every copied particle (matched by
+id), and J, E, B at n (the block is large enough that neither its periodic
+wrap nor the particles left out reach n).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1204_0838_gb300 import pic, workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+HALF = 8  # block = node - 8 .. node + 7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    pic.lib()
+
+
+def _full(precision):
+    cfg = W.config("c1" if precision == "fp64" else "c2", start_step=900)
+    g = pic.Sim(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"], cfg["lambda0"],
+                x0=cfg["x0"], periodic_x=False, precision=precision, seed=cfg["seed"],
+                window=cfg["window"], track_ids=True)
+    g.add_species(cfg["prof_x"], cfg["prof_n"], cfg["ppc"], loading=cfg["loading"])
+    g.add_laser(cfg["a0"], cfg["waist"], cfg["fwhm"], cfg["lambda0"], cfg["x_focus"], cfg["t_peak"])
+    pic.pic_autotune(g.h, 1, None)
+    g.step(3)
+    return g, cfg
+
+
+def _block(a, n, shape):
+    """16^3 block of a full-size array centred on node n (y, z wrapped)."""
+    i = np.arange(n[0] - HALF, n[0] + HALF)
+    j = np.arange(n[1] - HALF, n[1] + HALF) % shape[1]
+    k = np.arange(n[2] - HALF, n[2] + HALF) % shape[2]
+    return a[np.ix_(i, j, k)]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_c1_full_size_sampled_parity(precision, tol):
+    g, cfg = _full(precision)
+    shape = (cfg["nx"], cfg["ny"], cfg["nz"])
+    F0 = [g.field(c) for c in range(6)]
+    P0 = g.particles()
+    s0 = g.info()["shifts"]
+    g.step(1)
+    ds = g.info()["shifts"] - s0  # the window moved: post-step state is ds cells back
+    assert ds == 1
+    P1 = g.particles()
+    order1 = np.argsort(P1["id"])
+    ids1 = P1["id"][order1]
+    J1 = [g.field(c) for c in (6, 7, 8)]
+    F1 = [g.field(c) for c in range(6)]
+    cells0 = np.floor(P0["xi"]).astype(np.int64)
+
+    rng = np.random.default_rng(20)
+    # sample nodes inside the plasma, near the laser (last third of the window)
+    occupied = cells0[:, rng.integers(0, cells0.shape[1], 4000)]
+    cand = occupied[:, (occupied[0] > shape[0] * 2 // 3) & (occupied[0] < shape[0] - 12)]
+    assert cand.shape[1] > 8
+    nodes = cand[:, rng.choice(cand.shape[1], 6, replace=False)].T
+    checked = 0
+    for n in nodes:
+        # particles whose start cell is within [n-4, n+3] on every axis (y, z periodic)
+        d = cells0 - n[:, None]
+        d[1] = (d[1] + shape[1] // 2) % shape[1] - shape[1] // 2
+        d[2] = (d[2] + shape[2] // 2) % shape[2] - shape[2] // 2
+        sel = np.all((d >= -4) & (d <= 3), axis=0)
+        assert sel.sum() > 0
+        o = O.Sim(16, 16, 16, cfg["dx"], cfg["dy"], cfg["dz"], cfg["lambda0"], periodic_x=True)
+        for c in range(6):
+            o.field(c)[...] = _block(F0[c], n, shape)
+        xi_local = P0["xi"][:, sel] - (n - HALF)[:, None]
+        for a in (1, 2):
+            xi_local[a] = (xi_local[a] + shape[a] // 2 - HALF) % shape[a] - shape[a] // 2 + HALF
+        o.set_particles(xi_local, P0["u"][:, sel], P0["w"][sel], P0["id"][sel])
+        o.step(1)
+        po = o.particles()
+        # particles: by id against the GPU's full-size step
+        pos = np.searchsorted(ids1, po["id"])
+        assert np.array_equal(ids1[pos], po["id"])
+        gi = order1[pos]
+        u_g = P1["u"][:, gi]
+        xi_g = P1["xi"][:, gi] - (n - HALF)[:, None]
+        xi_g[0] += ds
+        for a in (1, 2):
+            xi_g[a] = (xi_g[a] + shape[a] // 2 - HALF) % shape[a] - shape[a] // 2 + HALF
+        uscale = max(1.0, np.abs(po["u"]).max())
+        assert np.abs(u_g - po["u"]).max() <= tol * uscale
+        dxi = np.abs(xi_g - po["xi"])
+        dxi = np.minimum(dxi, 16 - dxi)  # the oracle box wraps
+        assert dxi.max() <= tol * 16
+        # J, E, B at the sampled node (post-step arrays are in the shifted frame)
+        m = (n[0] - ds, n[1], n[2])
+        for c, arr in zip((6, 7, 8), J1):
+            ref = o.field(c)[HALF, HALF, HALF]
+            scale = max(np.abs(o.field(c)[HALF - 1:HALF + 2, HALF - 1:HALF + 2, HALF - 1:HALF + 2]).max(), 1e-30)
+            assert abs(arr[m] - ref) <= tol * scale, ("J", c, arr[m], ref)
+        for c in range(6):
+            ref = o.field(c)[HALF, HALF, HALF]
+            scale = max(np.abs(o.field(c)[HALF - 2:HALF + 3, HALF, HALF]).max(), 1e-30)
+            assert abs(F1[c][m] - ref) <= tol * scale, ("F", c, F1[c][m], ref)
+        checked += 1
+    assert checked == len(nodes)
+    g.close()

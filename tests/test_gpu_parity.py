@@ -28,9 +28,10 @@ def _cuda():
     pic.lib()
 
 
-def _pair(shape, periodic, dx=LAM / 8, dy=LAM / 3, dz=LAM / 2, precision="fp64"):
-    g = pic.Sim(*shape, dx, dy, dz, LAM, periodic_x=periodic, precision=precision, track_ids=True)
-    o = O.Sim(*shape, dx, dy, dz, LAM, periodic_x=periodic)
+def _pair(shape, periodic, dx=LAM / 8, dy=LAM / 3, dz=LAM / 2, precision="fp64", solver="perfect"):
+    g = pic.Sim(*shape, dx, dy, dz, LAM, periodic_x=periodic, precision=precision, track_ids=True,
+                solver=solver)
+    o = O.Sim(*shape, dx, dy, dz, LAM, periodic_x=periodic, solver=solver)
     return g, o
 
 
@@ -295,3 +296,36 @@ def test_autotune_restores_state_and_keeps_results(tmp_path):
     o.step(2)
     compare_particles(g.particles(), o.particles(), 1e-10)
     compare_fields(g, o, 1e-10)
+
+
+# ---------------------------------------------------------------------------
+# normal-dispersion (Yee) variant
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("periodic,shape", [(True, (32, 16, 16)), (False, (48, 16, 8))])
+def test_yee_variant_one_step_parity(periodic, shape):
+    g, o = _pair(shape, periodic, solver="yee")
+    assert g.info()["dt"] < g.info()["dx"]
+    _set_random(g, o, shape, 20000, seed=12, periodic=periodic)
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+
+
+def test_yee_window_moves_at_c_with_fractional_shifts():
+    cfg = _window_cfg()
+    g = pic.Sim(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"], cfg["lambda0"],
+                x0=cfg["x0"], periodic_x=False, seed=cfg["seed"], window=cfg["window"],
+                track_ids=True, solver="yee")
+    o = O.Sim(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"], cfg["lambda0"],
+              x0=cfg["x0"], periodic_x=False, seed=cfg["seed"], window=cfg["window"], solver="yee")
+    for s in (g, o):
+        s.add_species(cfg["prof_x"], cfg["prof_n"], cfg["ppc"], loading=cfg["loading"])
+        s.add_laser(cfg["a0"], cfg["waist"], cfg["fwhm"], cfg["lambda0"], cfg["x_focus"], cfg["t_peak"])
+    g.step(40)
+    o.step(40)
+    ig, io = g.info(), o.info()
+    assert ig["shifts"] == io["shifts"] < 40  # c dt < dx: not every step shifts
+    assert ig["np"] == io["np"]
+    _compare_diags(_diags(g, cfg["nx"]), _diags(o, cfg["nx"]), 1e-6)

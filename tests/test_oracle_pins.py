@@ -130,10 +130,11 @@ def test_constraint_dx_le_dy_dz_enforced():
 # ---------------------------------------------------------------------------
 # Field solver: discrete dispersion relation for oblique waves
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("solver", ["perfect", "yee"])
 @pytest.mark.parametrize("mx,my", [(1, 0), (3, 0), (1, 1), (2, 3), (5, 2)])
-def test_field_solver_matches_dispersion_relation(mx, my):
+def test_field_solver_matches_dispersion_relation(mx, my, solver):
     nx, ny, nz = 16, 8, 4
-    s = _sim(nx, ny, nz, dx=LAM / 8, dy=LAM / 3, dz=LAM / 2)
+    s = _sim(nx, ny, nz, dx=LAM / 8, dy=LAM / 3, dz=LAM / 2, solver=solver)
     inf = s.info()
     dx, dy, dz, dt = inf["dx"], inf["dy"], inf["dz"], inf["dt"]
     kx, ky = 2 * np.pi * mx / (nx * dx), 2 * np.pi * my / (ny * dy)
@@ -148,8 +149,10 @@ def test_field_solver_matches_dispersion_relation(mx, my):
     N = 37
     s.step(N)
     assert np.allclose(s.field(O.EZ), ez0 * np.cos(N * omega * dt), atol=1e-12)
-    if my == 0:  # along x: exact vacuum dispersion omega = c k
+    if my == 0 and solver == "perfect":  # along x: exact vacuum dispersion omega = c k
         assert abs(omega - kx) < 1e-13
+    if solver == "yee":  # no smoothing: every stencil is the identity
+        assert np.allclose(coef, [[1, 0, 0, 0]] * 3)
 
 
 def test_field_solver_oblique_polarisation_x():
@@ -602,3 +605,56 @@ def test_relativistic_free_streaming_and_periodic_wrap():
     expect = (xi + N * inf["dt"] * u / (g * d)) % n
     assert np.allclose(p["xi"], expect, atol=1e-12)
     assert np.allclose(p["u"], u, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# Perfect vs normal (Yee) dispersion: group velocity of a pulse along x
+# (Sec. 1: FDTD's axial dispersion slows the driver; Sec. 2: the smoothed
+# curl removes it; Sec. 3.3 compares the two)
+# ---------------------------------------------------------------------------
+def _pulse_centroid_speed(solver, steps=300):
+    nx, ny, nz = 512, 4, 4
+    dx = LAM / 8
+    s = O.Sim(nx, ny, nz, dx, LAM / 2, LAM / 2, LAM, periodic_x=True, solver=solver)
+    inf = s.info()
+    L = nx * inf["dx"]
+    fwhm = 3 * LAM / C0
+    # envelope centre at a quarter of the box at t = 0
+    s.add_laser(1.0, 1e6, fwhm, LAM, x_focus=0.0, t_peak=-(L / 4) * LAM / (2 * np.pi) / C0)
+    x = np.arange(nx) * inf["dx"]
+
+    def centroid(center_guess):
+        e2 = s.field(O.EY)[:, 0, 0] ** 2
+        d = (x - center_guess + L / 2) % L - L / 2
+        m = np.abs(d) < L / 6
+        return center_guess + (d[m] * e2[m]).sum() / e2[m].sum()
+
+    c0 = centroid(L / 4)
+    s.step(steps)
+    t = steps * inf["dt"]
+    c1 = centroid(L / 4 + t)
+    return (c1 - c0) / t, inf
+
+
+def test_perfect_dispersion_pulse_moves_at_c():
+    v, _ = _pulse_centroid_speed("perfect")
+    assert abs(v - 1.0) < 1e-10
+
+
+def test_yee_pulse_is_slower_by_its_dispersion_relation():
+    v, inf = _pulse_centroid_speed("yee")
+    C = inf["dt"] / inf["dx"]
+    kdx = 2 * np.pi / 8  # carrier: 8 cells per wavelength
+    vg = np.cos(kdx / 2) / np.sqrt(1 - (C * np.sin(kdx / 2)) ** 2)
+    assert C < 1.0 and vg < 0.995
+    assert abs(v - vg) < 5e-4
+    assert v < 1.0 - 5e-3
+
+
+def test_yee_courant_limit_enforced():
+    lam = LAM
+    dx, dy = lam / 8, lam / 2
+    lim = 1 / np.sqrt(1 / dx ** 2 + 2 / dy ** 2)  # metres of c t
+    O.Sim(8, 8, 8, dx, dy, dy, lam, solver="yee", dt=0.999 * lim / C0)
+    with pytest.raises(ValueError):
+        O.Sim(8, 8, 8, dx, dy, dy, lam, solver="yee", dt=1.001 * lim / C0)
