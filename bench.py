@@ -58,6 +58,20 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_over_ranks(ms, pushed, world_size):
+    """Whole-job figures of N independent replicas: the slowest rank's time and
+    the particle-steps summed over ranks (no-op for one rank)."""
+    if world_size <= 1:
+        return float(ms), float(pushed)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(pushed)], dtype=torch.float64)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(c[0])
+
+
 def _workload(args):
     from paper_1204_0838_gb300 import workloads as W
     start = args.start_step
@@ -259,14 +273,7 @@ def run_ours(args):
     info = g.info()
     pushed = info["pushed"] - pushed0
     # max time / summed particle-steps over ranks
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
-        c = torch.tensor([float(pushed)], dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        pushed = float(c[0])
+    ms, pushed = reduce_over_ranks(ms, pushed, ws)
     value = pushed / (ms / 1e3)
 
     # end to end through the C-ABI: one pic_step per step plus the field
@@ -278,14 +285,8 @@ def run_ours(args):
         g.diag("field_energy")
     t1 = time.perf_counter()
     pushed_e = g.info()["pushed"] - pushed_e0
-    e2e = pushed_e / (t1 - t0)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t1 - t0], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([float(pushed_e)], dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        e2e = float(c[0]) / float(t[0])
+    te, pe = reduce_over_ranks(t1 - t0, pushed_e, ws)
+    e2e = pe / te
 
     peaks, src = _peaks()
     k2_ms = timing["ms"]["gather_push_deposit"]
@@ -380,13 +381,7 @@ def run_batch(args):
     clk = clocks.stop()
     ms = info["last_step_ms"]
     pushed = sum(g.info()["pushed"] for g in sims) - p0
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
-        c = torch.tensor([float(pushed)], dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        pushed = float(c[0])
+    ms, pushed = reduce_over_ranks(ms, pushed, ws)
     value = pushed / (ms / 1e3)
     t0 = time.perf_counter()
     pe0 = sum(g.info()["pushed"] for g in sims)

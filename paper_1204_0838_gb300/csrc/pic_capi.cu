@@ -360,13 +360,20 @@ Fields<T> curl_view(const pic_t* h) {
   return c;
 }
 
+// Launch of the tiled smoothed curl over window-relative slabs [i0, i0 + ni).
+template <typename T>
+void launch_curl(const pic_t* h, const Geom<T>& g, int mode, int i0, int ni, cudaStream_t s) {
+  const dim3 grid((ni + CB_X - 1) / CB_X, (h->ny + CB_Y - 1) / CB_Y, (h->nz + CB_Z - 1) / CB_Z);
+  k_curl_tiled<T><<<grid, 256, curl_tiled_smem_bytes<T>(), s>>>(g, smooth<T>(h), fields<T>(h), curl_view<T>(h),
+                                                               field_coef<T>(h), mode, i0, ni);
+}
+
 // C = curl'(E) over window-relative slabs [i0, i0 + ni).
 template <typename T>
 int curl_only(pic_t* h, int i0, int ni) {
   GroupTimer tm(h, G_FIELD);
   counted(h, G_FIELD);
-  k_curl_update<T><<<grid_for((long long)ni * h->ny * h->nz), 256, 0, h->stream>>>(
-      geom<T>(h), smooth<T>(h), fields<T>(h), curl_view<T>(h), field_coef<T>(h), 0, i0, ni);
+  launch_curl<T>(h, geom<T>(h), 0, i0, ni, h->stream);
   CK(h, cudaGetLastError());
   return PIC_OK;
 }
@@ -448,8 +455,7 @@ template <typename T>
 int field_second_half(pic_t* h) {
   GroupTimer tm(h, G_FIELD);
   counted(h, G_FIELD);
-  k_curl_update<T><<<grid_for(h->ncell), 256, 0, h->stream>>>(geom<T>(h), smooth<T>(h), fields<T>(h),
-                                                              curl_view<T>(h), field_coef<T>(h), 1, 0, h->nx);
+  launch_curl<T>(h, geom<T>(h), 1, 0, h->nx, h->stream);
   CK(h, cudaGetLastError());
   return PIC_OK;
 }
@@ -801,6 +807,11 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
     cudaError_t e = h->precision == PIC_FP64
                         ? cudaFuncSetAttribute(k_push_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)
                         : cudaFuncSetAttribute(k_push_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = h->precision == PIC_FP64 ? cudaFuncSetAttribute(k_curl_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)curl_tiled_smem_bytes<double>())
+                                   : cudaFuncSetAttribute(k_curl_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)curl_tiled_smem_bytes<float>());
     if (e != cudaSuccess) {
       cudaGetLastError();
       pic_destroy(h);
@@ -1475,11 +1486,12 @@ int enqueue_step_dyn(pic_t* h, cudaStream_t s, int cur, long long* kernels) {
                                                             (int)h->capacity, h->keys, h->tcnt, hq, (T)h->q, 0,
                                                             x_lo(h), x_hi(h), h->d_pushed, h->d_ctrl + 2);
   k_e_update<T><<<grid_for(n), 256, 0, s>>>(g, f, curl_view<T>(h), fc);
-  k_curl_update<T><<<grid_for(n), 256, 0, s>>>(g, S, f, curl_view<T>(h), fc, 1, 0, h->nx);
+  launch_curl<T>(h, g, 1, 0, h->nx, s);
   k_window_commit<<<1, 32, 0, s>>>(h->d_dyn);
   k_zero_front_slab<T><<<grid_for((long long)NCOMP * h->ny * h->nz), 256, 0, s>>>(gs, f);
-  k_curl_update<T><<<grid_for((long long)h->ny * h->nz), 256, 0, s>>>(gs, S, f, curl_view<T>(h), fc, 0, 0, 1);
-  k_curl_update<T><<<grid_for((long long)h->ny * h->nz), 256, 0, s>>>(gs, S, f, curl_view<T>(h), fc, 0, h->nx - 1, 1);
+  launch_curl<T>(h, gs, 0, 0, 1, s);
+  launch_curl<T>(h, gs, 0, h->nx - 1, 1, s);
+  (void)S;
   LoadSpec L;
   const bool inject = h->has_species;
   const long long nslot = (long long)h->ny * h->nz * std::max(h->ppc, 1);

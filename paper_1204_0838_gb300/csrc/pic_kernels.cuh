@@ -94,36 +94,13 @@ __global__ void __launch_bounds__(256) k_curl_e(Geom<T> g, Smooth<T> S, const T*
   }
 }
 
-// Eq. (perfDispMaxwell), electric step: E += dt (curl B - J), standard curl.
-template <typename T>
-__global__ void __launch_bounds__(256) k_curl_b(Geom<T> g, Fields<T> f) {
-  const int nyz = g.nyz;
-  const long long ncell = (long long)g.nx * nyz;
-  const T *Bx = f.c[BX], *By = f.c[BY], *Bz = f.c[BZ];
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q / nyz);
-    const int r = (int)(q - (long long)i * nyz);
-    const int j = r / g.nz, k = r - j * g.nz;
-    const int s = slab_of(g, i), sm = slab_of(g, i - 1);
-    const size_t id = (size_t)s * nyz + r;
-    const T bx = Bx[id], by = By[id], bz = Bz[id];
-    const T cx = (bz - ld(Bz, g, s, j - 1, k)) / g.dy - (by - ld(By, g, s, j, k - 1)) / g.dz;
-    const T cy = (bx - ld(Bx, g, s, j, k - 1)) / g.dz - (bz - ld(Bz, g, sm, j, k)) / g.dx;
-    const T cz = (by - ld(By, g, sm, j, k)) / g.dx - (bx - ld(Bx, g, s, j - 1, k)) / g.dy;
-    f.c[EX][id] += g.dt * (cx - f.c[JX][id]);
-    f.c[EY][id] += g.dt * (cy - f.c[JY][id]);
-    f.c[EZ][id] += g.dt * (cz - f.c[JZ][id]);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Field update with a cached smoothed curl.  The two magnetic half steps of
 // consecutive steps use the same curl'(E^{n+1}), so it is computed once per
 // step and kept in C:
 //   k_e_update:     B^{n+1/2} = B^n - (dt/2) C^n (formed on the fly),
 //                   E^{n+1} = E^n + dt (curl B^{n+1/2} - J)
-//   k_curl_update:  C^{n+1} = curl'(E^{n+1}),
+//   k_curl_tiled:   C^{n+1} = curl'(E^{n+1}),
 //                   B^{n+1} = (B^n - (dt/2) C^n) - (dt/2) C^{n+1}
 // Reciprocal spacings are precomputed (no divisions in the loops).
 // ---------------------------------------------------------------------------
@@ -169,37 +146,116 @@ __global__ void __launch_bounds__(256) k_e_update(Geom<T> g, Fields<T> f, Fields
   }
 }
 
-// Smoothed curl of E at one cell (Sec. 2: D_i replaced by D_i S_i).
+// ---------------------------------------------------------------------------
+// Smoothed curl, shared-memory tiled.  A CTA covers a block of CB_X x CB_Y x
+// CB_Z cells (window-relative slabs i0 + blockIdx.x * CB_X ...).  It stages E
+// over the block plus one cell on every side, evaluates each of the six
+// smoothed fields (S_x Ey, S_x Ez over x = i .. i+CB_X; S_y Ez, S_y Ex over
+// y = j .. j+CB_Y; S_z Ex, S_z Ey over z = k .. k+CB_Z) once per point, and
+// forms curl'(E) from their differences.
+// mode 0: C = curl'(E) only (start, after E changed outside a step, or the
+//         slabs next to a moved window edge), over window-relative slabs
+//         [i0, i0 + ni);
+// mode 1: C^{n+1} = curl'(E^{n+1}) and the two B half steps.
+// ---------------------------------------------------------------------------
+constexpr int CB_X = 4, CB_Y = 8, CB_Z = 32;
+constexpr int CE_X = CB_X + 2, CE_Y = CB_Y + 2, CE_Z = CB_Z + 2;  // staged E extents
+constexpr int CE_N = CE_X * CE_Y * CE_Z;
+// smoothed-field extents
+constexpr int SXN = (CB_X + 1) * CB_Y * CB_Z;  // S_x Ey, S_x Ez
+constexpr int SYN = CB_X * (CB_Y + 1) * CB_Z;  // S_y Ez, S_y Ex
+constexpr int SZN = CB_X * CB_Y * (CB_Z + 1);  // S_z Ex, S_z Ey
+
 template <typename T>
-__device__ __forceinline__ void curl_smoothed(const Geom<T>& g, const Smooth<T>& S, const FieldCoef<T>& fc,
-                                              const T* Ex, const T* Ey, const T* Ez, int sm, int s, int sp, int j,
-                                              int k, T& cx, T& cy, T& cz) {
-  cx = (smooth_y(Ez, g, S, sm, s, sp, j + 1, k) - smooth_y(Ez, g, S, sm, s, sp, j, k)) * fc.idy -
-       (smooth_z(Ey, g, S, sm, s, sp, j, k + 1) - smooth_z(Ey, g, S, sm, s, sp, j, k)) * fc.idz;
-  cy = (smooth_z(Ex, g, S, sm, s, sp, j, k + 1) - smooth_z(Ex, g, S, sm, s, sp, j, k)) * fc.idz -
-       (smooth_x(Ez, g, S, sp, j, k) - smooth_x(Ez, g, S, s, j, k)) * fc.idx;
-  cz = (smooth_x(Ey, g, S, sp, j, k) - smooth_x(Ey, g, S, s, j, k)) * fc.idx -
-       (smooth_y(Ex, g, S, sm, s, sp, j + 1, k) - smooth_y(Ex, g, S, sm, s, sp, j, k)) * fc.idy;
+size_t curl_tiled_smem_bytes() {
+  return sizeof(T) * (3 * (size_t)CE_N + 2 * (size_t)(SXN + SYN + SZN));
 }
 
-// mode 0: C = curl'(E) only (start, or after E changed outside a step), over
-//         window-relative slabs [i0, i0 + ni);
-// mode 1: C^{n+1} = curl'(E^{n+1}) and the two B half steps, whole grid.
 template <typename T>
-__global__ void __launch_bounds__(256) k_curl_update(Geom<T> g, Smooth<T> S, Fields<T> f, Fields<T> cc,
-                                                    FieldCoef<T> fc, int mode, int i0, int ni) {
+__global__ void __launch_bounds__(256) k_curl_tiled(Geom<T> g, Smooth<T> S, Fields<T> f, Fields<T> cc,
+                                                   FieldCoef<T> fc, int mode, int i0, int ni) {
   if (!dyn_prologue(g)) return;
-  const int nyz = g.nyz;
-  const long long ncell = (long long)ni * nyz;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int i = i0 + (int)(q / nyz);
-    const int r = (int)(q - (long long)(i - i0) * nyz);
-    const int j = r / g.nz, k = r - j * g.nz;
-    const int s = slab_of(g, i), sm = slab_of(g, i - 1), sp = slab_of(g, i + 1);
-    T cx, cy, cz;
-    curl_smoothed(g, S, fc, f.c[EX], f.c[EY], f.c[EZ], sm, s, sp, j, k, cx, cy, cz);
-    const size_t id = (size_t)s * nyz + r;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sE = reinterpret_cast<T*>(smem_raw);  // [3][CE_X][CE_Y][CE_Z], origin (bx-1, by-1, bz-1)
+  T* sSxEy = sE + 3 * CE_N;                // [CB_X+1][CB_Y][CB_Z]
+  T* sSxEz = sSxEy + SXN;
+  T* sSyEz = sSxEz + SXN;                  // [CB_X][CB_Y+1][CB_Z]
+  T* sSyEx = sSyEz + SYN;
+  T* sSzEx = sSyEx + SYN;                  // [CB_X][CB_Y][CB_Z+1]
+  T* sSzEy = sSzEx + SZN;
+  const int bx = i0 + blockIdx.x * CB_X, by = blockIdx.y * CB_Y, bz = blockIdx.z * CB_Z;
+  const int tid = threadIdx.x;
+
+  // stage E with a one-cell halo (zero outside an open window)
+  for (int q = tid; q < CE_N; q += blockDim.x) {
+    const int lz = q % CE_Z, r = q / CE_Z;
+    const int ly = r % CE_Y, lx = r / CE_Y;
+    const int s = slab_of(g, bx - 1 + lx);
+    const int j = wrapi(by - 1 + ly, g.ny), k = wrapi(bz - 1 + lz, g.nz);  // blocks may exceed small ny, nz
+    const size_t gi = (size_t)(s < 0 ? 0 : s) * g.nyz + (size_t)j * g.nz + k;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sE[c * CE_N + q] = s < 0 ? T(0) : f.c[EX + c][gi];
+  }
+  __syncthreads();
+
+  auto E = [&](int c, int lx, int ly, int lz) -> T { return sE[c * CE_N + (lx * CE_Y + ly) * CE_Z + lz]; };
+  // S_x at staged (lx, ly, lz): smoothing in y and z
+  auto sx = [&](int c, int lx, int ly, int lz) -> T {
+    const T ctr = E(c, lx, ly, lz);
+    const T ey = E(c, lx, ly + 1, lz) + E(c, lx, ly - 1, lz);
+    const T ez = E(c, lx, ly, lz + 1) + E(c, lx, ly, lz - 1);
+    const T cr = E(c, lx, ly + 1, lz + 1) + E(c, lx, ly + 1, lz - 1) + E(c, lx, ly - 1, lz + 1) + E(c, lx, ly - 1, lz - 1);
+    return S.a[0] * ctr + S.b1[0] * ey + S.b2[0] * ez + S.g[0] * cr;
+  };
+  auto sy = [&](int c, int lx, int ly, int lz) -> T {  // smoothing in x and z
+    const T ctr = E(c, lx, ly, lz);
+    const T ex = E(c, lx + 1, ly, lz) + E(c, lx - 1, ly, lz);
+    const T ez = E(c, lx, ly, lz + 1) + E(c, lx, ly, lz - 1);
+    const T cr = E(c, lx + 1, ly, lz + 1) + E(c, lx + 1, ly, lz - 1) + E(c, lx - 1, ly, lz + 1) + E(c, lx - 1, ly, lz - 1);
+    return S.a[1] * ctr + S.b1[1] * ex + S.b2[1] * ez + S.g[1] * cr;
+  };
+  auto sz = [&](int c, int lx, int ly, int lz) -> T {  // smoothing in x and y
+    const T ctr = E(c, lx, ly, lz);
+    const T ex = E(c, lx + 1, ly, lz) + E(c, lx - 1, ly, lz);
+    const T ey = E(c, lx, ly + 1, lz) + E(c, lx, ly - 1, lz);
+    const T cr = E(c, lx + 1, ly + 1, lz) + E(c, lx + 1, ly - 1, lz) + E(c, lx - 1, ly + 1, lz) + E(c, lx - 1, ly - 1, lz);
+    return S.a[2] * ctr + S.b1[2] * ex + S.b2[2] * ey + S.g[2] * cr;
+  };
+  // each smoothed value once (block-local coordinates; staged = local + 1)
+  for (int q = tid; q < SXN; q += blockDim.x) {
+    const int lz = q % CB_Z, r = q / CB_Z;
+    const int ly = r % CB_Y, lx = r / CB_Y;
+    sSxEy[q] = sx(1, lx + 1, ly + 1, lz + 1);
+    sSxEz[q] = sx(2, lx + 1, ly + 1, lz + 1);
+  }
+  for (int q = tid; q < SYN; q += blockDim.x) {
+    const int lz = q % CB_Z, r = q / CB_Z;
+    const int ly = r % (CB_Y + 1), lx = r / (CB_Y + 1);
+    sSyEz[q] = sy(2, lx + 1, ly + 1, lz + 1);
+    sSyEx[q] = sy(0, lx + 1, ly + 1, lz + 1);
+  }
+  for (int q = tid; q < SZN; q += blockDim.x) {
+    const int lz = q % (CB_Z + 1), r = q / (CB_Z + 1);
+    const int ly = r % CB_Y, lx = r / CB_Y;
+    sSzEx[q] = sz(0, lx + 1, ly + 1, lz + 1);
+    sSzEy[q] = sz(1, lx + 1, ly + 1, lz + 1);
+  }
+  __syncthreads();
+
+  const int cells = CB_X * CB_Y * CB_Z;
+  for (int q = tid; q < cells; q += blockDim.x) {
+    const int lz = q % CB_Z, r = q / CB_Z;
+    const int ly = r % CB_Y, lx = r / CB_Y;
+    const int i = bx + lx, j = by + ly, k = bz + lz;
+    if (i >= i0 + ni || j >= g.ny || k >= g.nz) continue;
+    const int x0 = (lx * CB_Y + ly) * CB_Z + lz, x1 = ((lx + 1) * CB_Y + ly) * CB_Z + lz;
+    const int y0 = (lx * (CB_Y + 1) + ly) * CB_Z + lz, y1 = (lx * (CB_Y + 1) + ly + 1) * CB_Z + lz;
+    const int z0 = (lx * CB_Y + ly) * (CB_Z + 1) + lz;
+    // Bx: D_y S_y Ez - D_z S_z Ey; By: D_z S_z Ex - D_x S_x Ez; Bz: D_x S_x Ey - D_y S_y Ex
+    const T cx = (sSyEz[y1] - sSyEz[y0]) * fc.idy - (sSzEy[z0 + 1] - sSzEy[z0]) * fc.idz;
+    const T cy = (sSzEx[z0 + 1] - sSzEx[z0]) * fc.idz - (sSxEz[x1] - sSxEz[x0]) * fc.idx;
+    const T cz = (sSxEy[x1] - sSxEy[x0]) * fc.idx - (sSyEx[y1] - sSyEx[y0]) * fc.idy;
+    const size_t id = (size_t)slab_of(g, i) * g.nyz + (size_t)j * g.nz + k;
     if (mode == 1) {
       f.c[BX][id] = (f.c[BX][id] - fc.hdt * cc.c[0][id]) - fc.hdt * cx;
       f.c[BY][id] = (f.c[BY][id] - fc.hdt * cc.c[1][id]) - fc.hdt * cy;

