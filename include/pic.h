@@ -70,6 +70,14 @@ extern "C" {
 #define PIC_DIAG_CHARGE 2       /* len >= 1: sum |q| w over gamma > a->gamma_min, C  */
 #define PIC_DIAG_SPECTRUM 3     /* len = bins: charge per bin of (gamma-1) m c^2 in
                                    [a->e_min, a->e_max) MeV, C                     */
+#define PIC_DIAG_EMITTANCE 4    /* len >= 2: normalised rms emittance (Sec. 3.2 formula)
+                                   in y and z of the particles with gamma >
+                                   a->gamma_min, metres (x 1e6 = mm mrad); transverse
+                                   positions taken from the box axis                 */
+#define PIC_DIAG_PHASE_X_PX 5   /* len = nx * bins: charge per (window x cell, p_x bin),
+                                   p_x / (m c) in [a->p_min, a->p_max), C (Fig. 3)     */
+#define PIC_DIAG_DENSITY_XY 6   /* len >= nx * ny: electron density in the z = nz/2 cell
+                                   plane, [i][j], units of n_c (Fig. 2)               */
 #define PIC_FLAG_TRACK_IDS 1u   /* carry a 32-bit id per particle (tests, tracking) */
 
 /* Optional device-memory hooks (e.g. a framework's caching allocator).
@@ -117,8 +125,9 @@ typedef struct pic_laser_opts {
 } pic_laser_opts;
 
 typedef struct pic_diag_args {
-  double gamma_min;    /* PIC_DIAG_CHARGE threshold (e.g. 20)                */
+  double gamma_min;    /* PIC_DIAG_CHARGE / PIC_DIAG_EMITTANCE threshold     */
   double e_min, e_max; /* PIC_DIAG_SPECTRUM range, MeV                       */
+  double p_min, p_max; /* PIC_DIAG_PHASE_X_PX range of p_x / (m c)           */
 } pic_diag_args;
 
 typedef struct pic_info {
@@ -224,8 +233,9 @@ int pic_destroy(pic_t* h);
  * must not allocate after set-up -- a host framework with a fixed device
  * memory budget, a latency-critical loop where cudaMalloc/cudaFree would
  * synchronise the device, code running inside another library's callbacks --
- * use pic_diag_noalloc instead: same kinds, arguments, units and results as
- * pic_diag, with the reduction scratch in a fixed file-scope device array of
+ * use pic_diag_noalloc instead: the kinds EX_LINEOUT, FIELD_ENERGY, CHARGE and
+ * SPECTRUM, with the same arguments, units and results as pic_diag (other
+ * kinds return PIC_ERR_ARG), and the reduction scratch in a fixed file-scope device array of
  * PIC_NOALLOC_MAX_LEN doubles (512 KiB, present on every GPU that loads the
  * library until it is unloaded).  It calls no cudaMalloc, cudaFree or other
  * allocating routine.  Results longer than PIC_NOALLOC_MAX_LEN values (a

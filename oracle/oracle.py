@@ -15,7 +15,8 @@ EX, EY, EZ, BX, BY, BZ, JX, JY, JZ = range(9)
 COMP_NAMES = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz"]
 LOAD = {"random": 0, "lattice": 1}
 LASER = {"auto": 0, "hard_source": 1, "in_box": 2}
-DIAG = {"ex_lineout": 0, "field_energy": 1, "charge": 2, "spectrum": 3, "dive_residual": 4}
+DIAG = {"ex_lineout": 0, "field_energy": 1, "charge": 2, "spectrum": 3, "dive_residual": 4,
+        "emittance": 5, "phase_x_px": 6, "density_xy": 7}
 
 
 class _Grid(C.Structure):

@@ -853,6 +853,63 @@ int or_diag(or_sim* s, int kind, double* out, size_t len, double p0, double p1) 
       }
       return 0;
     }
+    case OR_DIAG_EMITTANCE: {
+      /* Sec. 3.2: eps_N,i = (m_e c)^-1 [(<p_i^2> - <p_i>^2)(<r_i^2> - <r_i>^2)
+       * - (<p_i r_i> - <r_i><p_i>)^2]^(1/2), averages weighted by the
+       * macroparticle weights, over particles with gamma > p0; r_i measured
+       * from the box axis.  Result in metres (x 1e6 = mm mrad). */
+      if (len < 2) return -1;
+      for (int ax = 1; ax <= 2; ++ax) {
+        double W = 0, su = 0, suu = 0, sr = 0, srr = 0, sur = 0;
+        const double d = ax == 1 ? s->dy : s->dz;
+        const int N = ax == 1 ? s->ny : s->nz;
+        for (size_t p = 0; p < s->np; ++p) {
+          double g = sqrt(1.0 + s->u[0][p] * s->u[0][p] + s->u[1][p] * s->u[1][p] + s->u[2][p] * s->u[2][p]);
+          if (!(g > p0)) continue;
+          double w = s->w[p], u = s->u[ax][p], r = (s->xi[ax][p] - 0.5 * N) * d;
+          W += w;
+          su += w * u;
+          suu += w * u * u;
+          sr += w * r;
+          srr += w * r * r;
+          sur += w * u * r;
+        }
+        double e = 0.0;
+        if (W > 0) {
+          double mu = su / W, mr = sr / W;
+          double det = (suu / W - mu * mu) * (srr / W - mr * mr) - (sur / W - mu * mr) * (sur / W - mu * mr);
+          e = det > 0 ? sqrt(det) : 0.0;
+        }
+        out[ax - 1] = e * Lunit;
+      }
+      return 0;
+    }
+    case OR_DIAG_PHASE_X_PX: {
+      /* charge per (window x cell, p_x bin), p_x / (m c) in [p0, p1) */
+      if (len < (size_t)s->nx || len % (size_t)s->nx || !(p1 > p0)) return -1;
+      size_t nb = len / (size_t)s->nx;
+      for (size_t b = 0; b < len; ++b) out[b] = 0.0;
+      for (size_t p = 0; p < s->np; ++p) {
+        double ux = s->u[0][p];
+        if (ux < p0 || ux >= p1) continue;
+        size_t b = (size_t)floor((ux - p0) / (p1 - p0) * (double)nb);
+        if (b >= nb) b = nb - 1;
+        int i = (int)floor(s->xi[0][p]);
+        out[(size_t)i * nb + b] += fabs(s->q) * s->w[p] * Qunit;
+      }
+      return 0;
+    }
+    case OR_DIAG_DENSITY_XY: {
+      /* electron density (units of n_c) in the z = nz/2 cell plane, [i][j] */
+      if (len < (size_t)s->nx * s->ny) return -1;
+      for (size_t b = 0; b < (size_t)s->nx * s->ny; ++b) out[b] = 0.0;
+      for (size_t p = 0; p < s->np; ++p) {
+        if ((int)floor(s->xi[2][p]) != s->nz / 2) continue;
+        int i = (int)floor(s->xi[0][p]), j = (int)floor(s->xi[1][p]);
+        out[(size_t)i * s->ny + j] += s->w[p] / (s->dx * s->dy * s->dz);
+      }
+      return 0;
+    }
     case OR_DIAG_DIVE_RESIDUAL: {
       if (len < 1) return -1;
       double* div = (double*)malloc(ncell * sizeof(double));

@@ -34,7 +34,8 @@ enum { OR_LOAD_RANDOM = 0, OR_LOAD_LATTICE = 1 };
 enum { OR_LASER_AUTO = 0, OR_LASER_HARD_SOURCE = 1, OR_LASER_IN_BOX = 2 };
 enum {
   OR_DIAG_EX_LINEOUT = 0, OR_DIAG_FIELD_ENERGY = 1, OR_DIAG_CHARGE = 2,
-  OR_DIAG_SPECTRUM = 3, OR_DIAG_DIVE_RESIDUAL = 4
+  OR_DIAG_SPECTRUM = 3, OR_DIAG_DIVE_RESIDUAL = 4, OR_DIAG_EMITTANCE = 5,
+  OR_DIAG_PHASE_X_PX = 6, OR_DIAG_DENSITY_XY = 7
 };
 
 typedef struct {

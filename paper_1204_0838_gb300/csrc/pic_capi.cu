@@ -631,7 +631,7 @@ int diag_impl(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* 
   const double nc = kEps0 * kMe * omega0 * omega0 / (kQe * kQe);
   const double Qunit = kQe * nc * Lunit * Lunit * Lunit;
   const double mc2 = kMe * kC * kC / (kQe * 1e6) * h->m;
-  size_t need = std::max<size_t>(len, 1);
+  size_t need = std::max<size_t>(std::max<size_t>(len, 11), (size_t)h->nx * h->ny);
   if (need > h->diag_cap) {
     dfree(h, h->d_diag);
     h->d_diag = (double*)dalloc(h, need * sizeof(double));
@@ -673,6 +673,57 @@ int diag_impl(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* 
             (int)len, h->d_diag);
       scale = std::fabs(h->q) * Qunit;
       nout = spec ? len : 1;
+      break;
+    }
+    case PIC_DIAG_EMITTANCE: {
+      if (len < 2) return fail(h, PIC_ERR_ARG, "emittance needs len >= 2");
+      if (!a) return fail(h, PIC_ERR_ARG, "diagnostic arguments required");
+      if (need < 11) return fail(h, PIC_ERR_ARG, "internal: scratch");
+      if (h->capacity > 0) {
+        counted(h, G_OTHER);
+        k_emittance_moments<T><<<grid_for(h->capacity, 256, 152 * 8), 256, 0, h->stream>>>(
+            g, parts<T>(h, h->cur), h->d_ctrl + h->cur, a->gamma_min, h->d_diag);
+      }
+      CK(h, cudaGetLastError());
+      double m[11];
+      CK(h, cudaMemcpyAsync(m, h->d_diag, sizeof(m), cudaMemcpyDeviceToHost, h->stream));
+      CK(h, cudaStreamSynchronize(h->stream));
+      for (int ax = 0; ax < 2; ++ax) {
+        double e = 0.0;
+        if (m[0] > 0) {
+          const double W = m[0];
+          const double mu = m[1 + 5 * ax] / W, mu2 = m[2 + 5 * ax] / W, mr = m[3 + 5 * ax] / W;
+          const double mr2 = m[4 + 5 * ax] / W, mur = m[5 + 5 * ax] / W;
+          const double var_u = mu2 - mu * mu, var_r = mr2 - mr * mr, cov = mur - mu * mr;
+          const double det = var_u * var_r - cov * cov;
+          e = det > 0 ? std::sqrt(det) : 0.0;
+        }
+        out[ax] = e * Lunit;  // normalised length -> metres (u is dimensionless)
+        if (!std::isfinite(out[ax])) return fail(h, PIC_ERR_NUMERIC, "diagnostic is not finite");
+      }
+      return PIC_OK;
+    }
+    case PIC_DIAG_PHASE_X_PX: {
+      if (!a || !(a->p_max > a->p_min)) return fail(h, PIC_ERR_ARG, "p_max <= p_min");
+      if (len < (size_t)h->nx || len % (size_t)h->nx) return fail(h, PIC_ERR_ARG, "len must be nx * bins");
+      if (h->capacity > 0) {
+        counted(h, G_OTHER);
+        k_phase_x_px<T><<<grid_for(h->capacity, 256, 152 * 8), 256, 0, h->stream>>>(
+            g, parts<T>(h, h->cur), h->d_ctrl + h->cur, a->p_min, a->p_max, (int)(len / h->nx), h->d_diag);
+      }
+      scale = std::fabs(h->q) * Qunit;
+      nout = len;
+      break;
+    }
+    case PIC_DIAG_DENSITY_XY: {
+      if (len < (size_t)h->nx * h->ny) return fail(h, PIC_ERR_ARG, "density map needs len >= nx * ny");
+      if (h->capacity > 0) {
+        counted(h, G_OTHER);
+        k_density_xy<T><<<grid_for(h->capacity, 256, 152 * 8), 256, 0, h->stream>>>(
+            g, parts<T>(h, h->cur), h->d_ctrl + h->cur, h->d_diag);
+      }
+      scale = 1.0 / (h->dx * h->dy * h->dz);  // weight per cell volume: n / n_c
+      nout = (size_t)h->nx * h->ny;
       break;
     }
     default:

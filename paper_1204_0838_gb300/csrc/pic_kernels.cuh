@@ -663,6 +663,76 @@ __global__ void k_lineout(Geom<T> g, const T* Ex, double* out) {
     out[i] = (double)Ex[(size_t)slab_of(g, i) * g.nyz + (size_t)(g.ny / 2) * g.nz + g.nz / 2];
 }
 
+// Weighted transverse moments of the particles with gamma > gmin for the
+// normalised emittance (Sec. 3.2): out[0] = sum w, then per axis y, z:
+// sum w u, w u^2, w r, w r^2, w u r with r the distance from the box axis
+// (normalised units).
+template <typename T>
+__global__ void __launch_bounds__(256) k_emittance_moments(Geom<T> g, Parts<T> p, const int* __restrict__ d_np,
+                                                          double gmin, double* out) {
+  const int n = *d_np;
+  double acc[11];
+#pragma unroll
+  for (int i = 0; i < 11; ++i) acc[i] = 0.0;
+  const double d[2] = {(double)g.dy, (double)g.dz};
+  const int nn[2] = {g.ny, g.nz};
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const double ux = p.u[0][q], uy = p.u[1][q], uz = p.u[2][q];
+    if (!(sqrt(1.0 + ux * ux + uy * uy + uz * uz) > gmin)) continue;
+    const double w = (double)p.w[q];
+    const int cell = p.cell[q];
+    const int r = cell % g.nyz;
+    const int cyz[2] = {r / g.nz, r % g.nz};
+    acc[0] += w;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const double uu = (double)p.u[1 + a][q];
+      const double rr = ((double)cyz[a] + (double)p.o[1 + a][q] - 0.5 * nn[a]) * d[a];
+      acc[1 + 5 * a] += w * uu;
+      acc[2 + 5 * a] += w * uu * uu;
+      acc[3 + 5 * a] += w * rr;
+      acc[4 + 5 * a] += w * rr * rr;
+      acc[5 + 5 * a] += w * uu * rr;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 11; ++i) {
+    const double v = block_sum(acc[i]);
+    if (threadIdx.x == 0) atomicAdd(out + i, v);
+  }
+}
+
+// Charge per (window x cell, p_x bin): out[i * nb + b].
+template <typename T>
+__global__ void k_phase_x_px(Geom<T> g, Parts<T> p, const int* __restrict__ d_np, double pmin, double pmax, int nb,
+                             double* out) {
+  const int n = *d_np;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const double ux = p.u[0][q];
+    if (!(ux >= pmin && ux < pmax)) continue;
+    int b = (int)floor((ux - pmin) / (pmax - pmin) * nb);
+    if (b >= nb) b = nb - 1;
+    int i = p.cell[q] / g.nyz - g.origin;
+    if (i < 0) i += g.nx;
+    atomicAdd(out + (size_t)i * nb + b, (double)p.w[q]);
+  }
+}
+
+// Electron weight per cell of the z = nz/2 plane: out[i * ny + j].
+template <typename T>
+__global__ void k_density_xy(Geom<T> g, Parts<T> p, const int* __restrict__ d_np, double* out) {
+  const int n = *d_np;
+  const int kz = g.nz / 2;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const int cell = p.cell[q];
+    const int r = cell % g.nyz;
+    if (r % g.nz != kz) continue;
+    int i = cell / g.nyz - g.origin;
+    if (i < 0) i += g.nx;
+    atomicAdd(out + (size_t)i * g.ny + r / g.nz, (double)p.w[q]);
+  }
+}
+
 // kind 0: sum of w over gamma > gmin into out[0]; kind 1: histogram of
 // (gamma - 1) * mc2 over [e0, e1) into nb bins.
 template <typename T>

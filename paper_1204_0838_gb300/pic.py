@@ -22,6 +22,7 @@ PIC_SOLVER_PERFECT, PIC_SOLVER_YEE = 0, 1
 PIC_LOAD_RANDOM, PIC_LOAD_LATTICE = 0, 1
 PIC_LASER_AUTO, PIC_LASER_HARD_SOURCE, PIC_LASER_IN_BOX = 0, 1, 2
 PIC_DIAG_EX_LINEOUT, PIC_DIAG_FIELD_ENERGY, PIC_DIAG_CHARGE, PIC_DIAG_SPECTRUM = 0, 1, 2, 3
+PIC_DIAG_EMITTANCE, PIC_DIAG_PHASE_X_PX, PIC_DIAG_DENSITY_XY = 4, 5, 6
 PIC_FLAG_TRACK_IDS = 1
 COMPONENTS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz"]
 
@@ -56,7 +57,8 @@ class pic_laser_opts(C.Structure):
 
 
 class pic_diag_args(C.Structure):
-    _fields_ = [("gamma_min", C.c_double), ("e_min", C.c_double), ("e_max", C.c_double)]
+    _fields_ = [("gamma_min", C.c_double), ("e_min", C.c_double), ("e_max", C.c_double),
+                ("p_min", C.c_double), ("p_max", C.c_double)]
 
 
 class pic_info(C.Structure):
@@ -219,9 +221,9 @@ def pic_step(h, n=1):
     _check(lib().pic_step(h, int(n)), "pic_step", h)
 
 
-def pic_diag(h, kind, length=1, gamma_min=0.0, e_min=0.0, e_max=0.0):
+def pic_diag(h, kind, length=1, gamma_min=0.0, e_min=0.0, e_max=0.0, p_min=0.0, p_max=0.0):
     out = np.zeros(max(int(length), 1))
-    a = pic_diag_args(float(gamma_min), float(e_min), float(e_max))
+    a = pic_diag_args(float(gamma_min), float(e_min), float(e_max), float(p_min), float(p_max))
     _check(lib().pic_diag(h, int(kind), _dp(out), out.size, C.byref(a)), "pic_diag", h)
     return out
 
@@ -229,7 +231,7 @@ def pic_diag(h, kind, length=1, gamma_min=0.0, e_min=0.0, e_max=0.0):
 def pic_diag_noalloc(h, kind, length=1, gamma_min=0.0, e_min=0.0, e_max=0.0):
     """pic_diag without any device allocation (scratch in a fixed device array)."""
     out = np.zeros(max(int(length), 1))
-    a = pic_diag_args(float(gamma_min), float(e_min), float(e_max))
+    a = pic_diag_args(float(gamma_min), float(e_min), float(e_max), 0.0, 0.0)
     _check(lib().pic_diag_noalloc(h, int(kind), _dp(out), out.size, C.byref(a)), "pic_diag_noalloc", h)
     return out
 
@@ -321,7 +323,7 @@ def pic_batch_step(b, n=1):
 
 def pic_batch_diag(b, instance, kind, length=1, gamma_min=0.0, e_min=0.0, e_max=0.0):
     out = np.zeros(max(int(length), 1))
-    a = pic_diag_args(float(gamma_min), float(e_min), float(e_max))
+    a = pic_diag_args(float(gamma_min), float(e_min), float(e_max), 0.0, 0.0)
     _check(lib().pic_batch_diag(b, int(instance), int(kind), _dp(out), out.size, C.byref(a)),
            "pic_batch_diag")
     return out
@@ -420,8 +422,16 @@ class Sim:
 
     def diag(self, kind, length=1, p0=0.0, p1=0.0):
         kinds = {"ex_lineout": PIC_DIAG_EX_LINEOUT, "field_energy": PIC_DIAG_FIELD_ENERGY,
-                 "charge": PIC_DIAG_CHARGE, "spectrum": PIC_DIAG_SPECTRUM}
+                 "charge": PIC_DIAG_CHARGE, "spectrum": PIC_DIAG_SPECTRUM,
+                 "emittance": PIC_DIAG_EMITTANCE, "phase_x_px": PIC_DIAG_PHASE_X_PX,
+                 "density_xy": PIC_DIAG_DENSITY_XY}
         k = kinds[kind]
+        if k == PIC_DIAG_EMITTANCE:
+            return pic_diag(self.h, k, 2, gamma_min=p0)
+        if k == PIC_DIAG_PHASE_X_PX:
+            return pic_diag(self.h, k, length, p_min=p0, p_max=p1)
+        if k == PIC_DIAG_DENSITY_XY:
+            return pic_diag(self.h, k, self.shape[0] * self.shape[1])
         if k == PIC_DIAG_EX_LINEOUT:
             return pic_diag(self.h, k, max(length, self.shape[0]))
         if k == PIC_DIAG_CHARGE:

@@ -329,3 +329,22 @@ def test_yee_window_moves_at_c_with_fractional_shifts():
     assert ig["shifts"] == io["shifts"] < 40  # c dt < dx: not every step shifts
     assert ig["np"] == io["np"]
     _compare_diags(_diags(g, cfg["nx"]), _diags(o, cfg["nx"]), 1e-6)
+
+
+def test_phase_space_diagnostics_parity():
+    cfg = _window_cfg()
+    g, o = make_gpu(cfg), make_oracle(cfg)
+    g.step(30)
+    o.step(30)
+    nx, ny = cfg["nx"], cfg["ny"]
+    for s in (g, o):
+        pass
+    eg, eo = g.diag("emittance", 2, 1.00001), o.diag("emittance", 2, 1.00001)
+    assert np.allclose(eg, eo, rtol=1e-6, atol=0)
+    pg = g.diag("phase_x_px", nx * 40, -0.2, 0.2)
+    po = o.diag("phase_x_px", nx * 40, -0.2, 0.2)
+    # a particle within rounding of a bin edge may change bins: allow a few
+    assert np.abs(pg - po).sum() <= 1e-3 * po.sum()
+    dg, do = g.diag("density_xy", nx * ny), o.diag("density_xy", nx * ny)
+    assert np.abs(dg - do).sum() <= 1e-3 * do.sum()
+    assert abs(dg.sum() / do.sum() - 1) < 1e-3

@@ -658,3 +658,92 @@ def test_yee_courant_limit_enforced():
     O.Sim(8, 8, 8, dx, dy, dy, lam, solver="yee", dt=0.999 * lim / C0)
     with pytest.raises(ValueError):
         O.Sim(8, 8, 8, dx, dy, dy, lam, solver="yee", dt=1.001 * lim / C0)
+
+
+# ---------------------------------------------------------------------------
+# Phase-space diagnostics (Sec. 3.2: emittance formula, Figs. 2 and 3)
+# ---------------------------------------------------------------------------
+def _emittance_sim(xi, u, w):
+    s = _sim(8, 16, 16, dx=LAM / 8, dy=LAM / 4, dz=LAM / 4)
+    s.set_particles(xi, u, w)
+    return s
+
+
+def test_emittance_three_point_closed_form():
+    """Three equal weights at the corners of a triangle of area A in (y, p_y)
+    have normalised emittance 2 A / (3 sqrt 3) (determinant of the weighted
+    covariance by Cauchy-Binet)."""
+    dy_m = LAM / 4
+    y_cells = np.array([8.0, 8.0 + 1.0, 8.0])  # positions (cells) about the axis
+    uy = np.array([0.0, 0.0, 2.0])
+    xi = np.stack([np.full(3, 4.5), y_cells, np.full(3, 8.0)])
+    u = np.stack([np.full(3, 50.0), uy, np.zeros(3)])  # gamma ~ 50
+    s = _emittance_sim(xi, u, np.ones(3))
+    eps = s.diag("emittance", 2, 10.0)
+    area = 0.5 * (1.0 * dy_m) * 2.0  # metres x (p/mc)
+    assert abs(eps[0] / (2 * area / (3 * np.sqrt(3))) - 1) < 1e-12
+    assert eps[1] == 0.0  # z: all at the same point
+    # translation and scaling behaviour
+    s2 = _emittance_sim(xi + np.array([[0.0], [2.0], [0.0]]), u + np.array([[0.0], [3.0], [0.0]]), np.ones(3))
+    assert abs(s2.diag("emittance", 2, 10.0)[0] / eps[0] - 1) < 1e-12
+    s3 = _emittance_sim(xi, u * np.array([[1.0], [4.0], [1.0]]), np.ones(3))
+    assert abs(s3.diag("emittance", 2, 10.0)[0] / eps[0] - 4) < 1e-12
+    # the gamma threshold selects: nothing above gamma = 100
+    assert np.all(s.diag("emittance", 2, 100.0) == 0.0)
+
+
+def test_emittance_of_a_correlated_line_is_zero():
+    n = 50
+    rng = np.random.default_rng(2)
+    y = rng.uniform(4, 12, n)
+    xi = np.stack([np.full(n, 4.5), y, rng.uniform(4, 12, n)])
+    u = np.stack([np.full(n, 30.0), 0.7 * (y - 8) + 0.1, np.zeros(n)])
+    eps = _emittance_sim(xi, u, rng.uniform(0.5, 1.5, n)).diag("emittance", 2, 2.0)
+    assert eps[0] < 1e-12 * LAM
+
+
+def test_phase_space_matches_numpy_histogram():
+    rng = np.random.default_rng(3)
+    n = 4000
+    nx = 8
+    xi = np.stack([rng.uniform(0, nx, n), rng.uniform(0, 16, n), rng.uniform(0, 16, n)])
+    u = np.stack([rng.normal(0, 2, n), np.zeros(n), np.zeros(n)])
+    w = rng.uniform(0.5, 1.5, n)
+    s = _emittance_sim(xi, u, w)
+    nb = 10
+    ph = s.diag("phase_x_px", nx * nb, -3.0, 3.0).reshape(nx, nb)
+    ref, _, _ = np.histogram2d(np.floor(xi[0]), u[0], bins=[np.arange(nx + 1), np.linspace(-3, 3, nb + 1)],
+                               weights=w)
+    qunit = s.diag("charge", 1, 0.0)[0] / w.sum()
+    assert np.allclose(ph, ref * qunit, rtol=1e-12, atol=0)
+
+
+def test_density_map_of_uniform_lattice_plasma():
+    nx, ny, nz = 16, 8, 8
+    s = O.Sim(nx, ny, nz, LAM / 16, LAM / 3, LAM / 3, LAM, periodic_x=False, seed=5)
+    s.add_species([-1.0, 1.0], [0.013, 0.013], 4, loading="lattice")
+    d = s.diag("density_xy", nx * ny).reshape(nx, ny)
+    filled = d[2:nx - 3]
+    assert np.allclose(filled, 0.013, rtol=1e-12)
+    assert np.all(d[:2] == 0) and np.all(d[nx - 3:] == 0)
+
+
+def test_accelerating_phase_length_reading():
+    from paper_1204_0838_gb300 import analysis
+    x = np.arange(200)
+    e = np.sin(2 * np.pi * (x + 0.5) / 100.0)  # negative on cells 50..99 (and 150..199)
+    assert analysis.accelerating_phase_length(e, 0.5) == 50 * 0.5
+    assert analysis.accelerating_phase_length(np.ones(5), 1.0) == 0.0
+
+
+def test_initial_cells_decode_loader_ids():
+    from paper_1204_0838_gb300 import analysis
+    nx, ny, nz, ppc = 16, 4, 6, 2
+    s = O.Sim(nx, ny, nz, LAM / 16, LAM / 3, LAM / 3, LAM, periodic_x=False, seed=5)
+    s.add_species([-1.0, 1.0], [0.01, 0.01], ppc, loading="lattice")
+    p = s.particles()
+    L, j, k, slot = analysis.initial_cells(p["id"], ppc, ny, nz)
+    assert np.array_equal(L, np.floor(p["xi"][0]).astype(int))
+    assert np.array_equal(j, np.floor(p["xi"][1]).astype(int))
+    assert np.array_equal(k, np.floor(p["xi"][2]).astype(int))
+    assert np.all((slot == 0) == (p["xi"][1] % 1 < 0.5))
