@@ -224,6 +224,16 @@ int pic_set_particles(pic_t* h, const pic_particles* p);
 int pic_timing_start(pic_t* h, int enable);
 int pic_timing_read(pic_t* h, pic_timing* out);
 
+/* ---- checkpoint / resume ----
+ * pic_save writes the dynamic state (fields in window-relative order,
+ * particles, step, window shifts, the FP64 window accumulator, the push
+ * count) to a binary file; pic_load reads it into a handle created with the
+ * same grid, window, species and laser calls (PIC_ERR_ARG if the grid,
+ * precision or ppc differ, PIC_ERR_STATE if the file is not a checkpoint).
+ * Both synchronise the stream and stage the state through host memory. */
+int pic_save(pic_t* h, const char* path);
+int pic_load(pic_t* h, const char* path);
+
 int pic_destroy(pic_t* h);
 
 /* ---- diagnostics that allocate nothing ----

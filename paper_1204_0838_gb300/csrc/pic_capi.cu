@@ -1171,6 +1171,114 @@ int pic_set_particles(pic_t* h, const pic_particles* p) {
   return PIC_OK;
 }
 
+namespace {
+struct CkptHeader {
+  char magic[8];  // "PICCKPT1"
+  int version, precision, nx, ny, nz, ppc, has_ids, pad;
+  long long step, shifts, np, pushed;
+  double win_frac;
+};
+}  // namespace
+
+int pic_save(pic_t* h, const char* path) {
+  if (!h || !path) return PIC_ERR_ARG;
+  if (h->batched) return fail(h, PIC_ERR_STATE, "handle is part of a batch");
+  int rc = check_device_error(h);
+  if (rc) return rc;
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, "PICCKPT1", 8);
+  hd.version = 1;
+  hd.precision = h->precision;
+  hd.nx = h->nx;
+  hd.ny = h->ny;
+  hd.nz = h->nz;
+  hd.ppc = h->ppc;
+  hd.has_ids = h->pb[0].id != nullptr;
+  hd.step = h->step;
+  hd.shifts = h->shifts;
+  hd.np = h->capacity > 0 ? h->np_host : 0;
+  hd.pushed = h->pushed_host;
+  hd.win_frac = h->win_frac;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(h, PIC_ERR_ARG, "cannot open checkpoint file for writing");
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+  std::vector<double> buf(h->ncell);
+  for (int c = 0; c < NCOMP && ok; ++c) {
+    rc = pic_get_field(h, c, buf.data());
+    ok = rc == PIC_OK && std::fwrite(buf.data(), sizeof(double), h->ncell, f) == h->ncell;
+  }
+  if (ok && hd.np > 0) {
+    std::vector<double> a(7 * (size_t)hd.np);
+    std::vector<uint32_t> ids(hd.has_ids ? hd.np : 0);
+    pic_particles pp;
+    pp.n = hd.np;
+    for (int d = 0; d < 3; ++d) {
+      pp.xi[d] = a.data() + d * hd.np;
+      pp.u[d] = a.data() + (3 + d) * hd.np;
+    }
+    pp.w = a.data() + 6 * hd.np;
+    pp.id = hd.has_ids ? ids.data() : nullptr;
+    rc = pic_get_particles(h, &pp);
+    ok = rc == PIC_OK && std::fwrite(a.data(), sizeof(double), a.size(), f) == a.size();
+    if (ok && hd.has_ids) ok = std::fwrite(ids.data(), sizeof(uint32_t), ids.size(), f) == ids.size();
+  }
+  if (std::fclose(f) != 0) ok = false;
+  if (!ok) return rc ? rc : fail(h, PIC_ERR_ARG, "writing the checkpoint failed");
+  return PIC_OK;
+}
+
+int pic_load(pic_t* h, const char* path) {
+  if (!h || !path) return PIC_ERR_ARG;
+  if (h->batched) return fail(h, PIC_ERR_STATE, "handle is part of a batch");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(h, PIC_ERR_ARG, "cannot open checkpoint file");
+  CkptHeader hd;
+  if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "PICCKPT1", 8) != 0 || hd.version != 1) {
+    std::fclose(f);
+    return fail(h, PIC_ERR_STATE, "not a checkpoint of this library");
+  }
+  if (hd.precision != h->precision || hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz || hd.ppc != h->ppc) {
+    std::fclose(f);
+    return fail(h, PIC_ERR_ARG, "checkpoint grid, precision or ppc differ from the handle");
+  }
+  std::vector<double> buf(h->ncell);
+  int rc = PIC_OK;
+  for (int c = 0; c < NCOMP && rc == PIC_OK; ++c) {
+    if (std::fread(buf.data(), sizeof(double), h->ncell, f) != h->ncell) rc = fail(h, PIC_ERR_STATE, "truncated checkpoint");
+    if (rc == PIC_OK) rc = pic_set_field(h, c, buf.data());
+  }
+  if (rc == PIC_OK) {
+    std::vector<double> a(7 * (size_t)hd.np);
+    std::vector<uint32_t> ids(hd.has_ids ? hd.np : 0);
+    if (std::fread(a.data(), sizeof(double), a.size(), f) != a.size() ||
+        (hd.has_ids && std::fread(ids.data(), sizeof(uint32_t), ids.size(), f) != ids.size()))
+      rc = fail(h, PIC_ERR_STATE, "truncated checkpoint");
+    if (rc == PIC_OK) {
+      pic_particles pp;
+      pp.n = hd.np;
+      for (int d = 0; d < 3; ++d) {
+        pp.xi[d] = a.data() + d * hd.np;
+        pp.u[d] = a.data() + (3 + d) * hd.np;
+      }
+      pp.w = a.data() + 6 * hd.np;
+      pp.id = hd.has_ids ? ids.data() : nullptr;
+      rc = pic_set_particles(h, &pp);
+    }
+  }
+  std::fclose(f);
+  if (rc) return rc;
+  h->step = hd.step;
+  h->shifts = hd.shifts;
+  h->win_frac = hd.win_frac;
+  h->curl_valid = false;
+  unsigned long long pushed = (unsigned long long)hd.pushed;
+  CK(h, cudaMemcpyAsync(h->d_pushed, &pushed, sizeof(pushed), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->pushed_host = hd.pushed;
+  return PIC_OK;
+}
+
 int pic_timing_start(pic_t* h, int enable) {
   if (!h) return PIC_ERR_ARG;
   CK(h, cudaStreamSynchronize(h->stream));

@@ -102,6 +102,8 @@ _SIGS = {
     "pic_destroy": (C.c_int, [C.c_void_p]),
     "pic_diag_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_size_t,
                                    C.POINTER(pic_diag_args)]),
+    "pic_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "pic_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "pic_timing_start": (C.c_int, [C.c_void_p, C.c_int]),
     "pic_timing_read": (C.c_int, [C.c_void_p, C.POINTER(pic_timing)]),
     "pic_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
@@ -291,6 +293,14 @@ def pic_set_particles(h, xi, u, w, ids=None):
         ids = np.ascontiguousarray(ids, dtype=np.uint32)
         p.id = ids.ctypes.data_as(C.POINTER(C.c_uint32))
     _check(lib().pic_set_particles(h, C.byref(p)), "pic_set_particles", h)
+
+
+def pic_save(h, path):
+    _check(lib().pic_save(h, str(path).encode()), "pic_save", h)
+
+
+def pic_load(h, path):
+    _check(lib().pic_load(h, str(path).encode()), "pic_load", h)
 
 
 def pic_timing_start(h, enable=True):

@@ -348,3 +348,23 @@ def test_phase_space_diagnostics_parity():
     dg, do = g.diag("density_xy", nx * ny), o.diag("density_xy", nx * ny)
     assert np.abs(dg - do).sum() <= 1e-3 * do.sum()
     assert abs(dg.sum() / do.sum() - 1) < 1e-3
+
+
+def test_checkpoint_resume_continues_the_run(tmp_path):
+    cfg = _window_cfg()
+    a = make_gpu(cfg)
+    a.step(10)
+    path = str(tmp_path / "state.ckpt")
+    pic.pic_save(a.h, path)
+    a.step(10)
+    b = make_gpu(cfg)  # same set-up calls; the checkpoint replaces the state
+    pic.pic_load(b.h, path)
+    assert b.info()["step"] == 10 and b.info()["shifts"] == 10
+    b.step(10)
+    ia, ib = a.info(), b.info()
+    assert (ia["step"], ia["shifts"], ia["np"], ia["pushed"]) == (ib["step"], ib["shifts"], ib["np"], ib["pushed"])
+    compare_particles(a.particles(), b.particles(), 1e-12)
+    compare_fields(a, b, 1e-12)
+    with pytest.raises(pic.PicError):  # a different grid is refused
+        c = pic.Sim(32, 8, 8, LAM / 8, LAM / 4, LAM / 2, LAM)
+        pic.pic_load(c.h, path)
