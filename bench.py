@@ -296,7 +296,7 @@ def run_ours(args):
     sm_clock = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     achieved = FLOP_PER_PARTICLE * per_launch_pushes / avg_s / 1e12 if avg_s > 0 else 0.0
     peak = _fp_peak_tflops(precision, peaks.get("sm_max_mhz", 2070.0))
-    roofline = {"kernel": "k_push_deposit (gather + Boris + Esirkepov deposit)",
+    roofline = {"kernel": "k_push_tiled (gather + Boris + Esirkepov deposit)",
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if peak else None, "traffic": None,
                 "peak_source": "derived: 152 SMs x %s FMA lanes x 2 flop x %.0f MHz max clock" % (

@@ -112,8 +112,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom
   const T jc[3] = {T(-1) / (g.dt * g.dy * g.dz), T(-1) / (g.dt * g.dx * g.dz), T(-1) / (g.dt * g.dx * g.dy)};
   const T third = T(1) / T(3);
 
-  for (int base = pbeg; base < pend; base += blockDim.x) {
-    const int pi = base + threadIdx.x;
+  // Lane order.  Particles that share a cell sit next to each other in a
+  // tile's list (loading and the stable scatter keep their order), so with
+  // consecutive lanes the deposit atomics of a warp hit each address twice.
+  // In FP64 the lanes of a warp take particles mrow apart instead, which
+  // removes those same-address collisions.  FP32 keeps consecutive lanes:
+  // there the gather's broadcast reads from the shared cells weigh more.
+  constexpr bool kSpread = sizeof(T) == 8;
+  const int ntile = pend - pbeg;
+  const int mrow = (ntile + 31) >> 5;
+  const int nloop = kSpread ? 32 * mrow : ntile;
+  for (int base = 0; base < nloop; base += blockDim.x) {
+    const int kk = base + threadIdx.x;
+    int pi = pbeg + kk;  // pi >= pend: no particle
+    if (kSpread) {
+      const int loc = (kk & 31) * mrow + (kk >> 5);  // blockDim.x is a multiple of 32
+      pi = (kk < nloop && loc < ntile) ? pbeg + loc : pend;
+    }
     int key = -2;
     if (pi < pend) {
       const int cell = p.cell[pi];
