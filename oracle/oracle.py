@@ -23,7 +23,7 @@ class _Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
                 ("lambda0", C.c_double), ("x0", C.c_double),
-                ("periodic_x", C.c_int), ("seed", C.c_uint64), ("solver", C.c_int)]
+                ("periodic_x", C.c_int), ("seed", C.c_uint64), ("solver", C.c_int), ("pml", C.c_int)]
 
 
 class _Window(C.Structure):
@@ -108,9 +108,9 @@ class Sim:
     """One oracle simulation (SI set-up, normalised state)."""
 
     def __init__(self, nx, ny, nz, dx, dy, dz, lambda0, x0=0.0, periodic_x=True, seed=12040838,
-                 dt=0.0, window=None, solver="perfect"):
+                 dt=0.0, window=None, solver="perfect", pml=0):
         g = _Grid(nx, ny, nz, dx, dy, dz, lambda0, x0, 1 if periodic_x else 0, seed,
-                  1 if solver == "yee" else 0)
+                  1 if solver == "yee" else 0, int(pml))
         w = None
         if window is not None:
             w = C.pointer(_Window(float(window[0]), float(window[1])))

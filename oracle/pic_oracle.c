@@ -75,7 +75,17 @@ struct or_sim {
   long long step, shifts;
   int has_window;
   double win_v, win_t0, win_frac;
+  /* transverse absorbing layers: pml cells at each y and z end, and the
+   * memory variables of the convolutional PML (see pml_coef) */
+  int pml;
+  double* psi[8];
 };
+
+/* Memory variables, one per stretched derivative (name: field it enters, axis):
+ * E update: d_y Bz in Ex, d_y Bx in Ez, d_z By in Ex, d_z Bx in Ey;
+ * B update (smoothed curl): D_y S_y Ez in Bx, D_y S_y Ex in Bz,
+ * D_z S_z Ey in Bx, D_z S_z Ex in By. */
+enum { PSI_EX_Y = 0, PSI_EZ_Y, PSI_EX_Z, PSI_EY_Z, PSI_CX_Y, PSI_CZ_Y, PSI_CX_Z, PSI_CY_Z };
 
 /* ------------------------------------------------------------------ */
 /* Cubic B-spline kernel M4 (abstract, Sec. 3.1 third-order splines):  */
@@ -165,14 +175,21 @@ static inline int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
-/* Value of a component array at storage index (i,j,k); y and z are periodic,
- * x is periodic or else zero outside the window. */
+/* Value of a component array at storage index (i,j,k).  x is periodic or
+ * else zero outside the window; y and z are periodic, or (with absorbing
+ * layers) zero outside the grid. */
 static double fv(const or_sim* s, const double* a, int i, int j, int k) {
   if (s->periodic_x)
     i = wrap(i, s->nx);
   else if (i < 0 || i >= s->nx)
     return 0.0;
-  return a[ix3(s, i, wrap(j, s->ny), wrap(k, s->nz))];
+  if (s->pml) {
+    if (j < 0 || j >= s->ny || k < 0 || k >= s->nz) return 0.0;
+  } else {
+    j = wrap(j, s->ny);
+    k = wrap(k, s->nz);
+  }
+  return a[ix3(s, i, j, k)];
 }
 
 static void fadd(or_sim* s, double* a, int i, int j, int k, double v) {
@@ -180,7 +197,39 @@ static void fadd(or_sim* s, double* a, int i, int j, int k, double v) {
     i = wrap(i, s->nx);
   else if (i < 0 || i >= s->nx)
     return; /* never reached for particles inside the allowed range */
-  a[ix3(s, i, wrap(j, s->ny), wrap(k, s->nz))] += v;
+  if (s->pml) {
+    if (j < 0 || j >= s->ny || k < 0 || k >= s->nz) return; /* never reached either */
+  } else {
+    j = wrap(j, s->ny);
+    k = wrap(k, s->nz);
+  }
+  a[ix3(s, i, j, k)] += v;
+}
+
+/* ------------------------------------------------------------------ */
+/* Transverse absorbing layers (Sec. 3.1: a 16-layer perfectly matched */
+/* layer surrounds the box transversely; the paper gives no form).     */
+/* Reading: a convolutional PML with kappa = 1 and no frequency shift  */
+/* (Roden & Gedney 2000).  In the outer L cells of y (and of z) each   */
+/* derivative d/dy of the field update becomes d/dy + psi, with        */
+/* psi <- b psi + a (d/dy F), b = exp(-sigma dt), a = b - 1, updated   */
+/* once per step at the derivative's time level.  sigma grows as the   */
+/* cube of the depth into the layer: sigma = sigma_max (depth / L)^3,  */
+/* sigma_max = 4 ln(1e6) / (2 L d) (normal-incidence reflection 1e-6   */
+/* of the continuous layer).  The smoothed derivatives D_y S_y of the  */
+/* perfect-dispersion curl are stretched the same way.  Depth, in      */
+/* cells, at position pos (nodes integer, half nodes + 1/2) of an axis */
+/* of n cells: max(L - pos, pos - (n - 1 - L), 0).                     */
+/* ------------------------------------------------------------------ */
+static void pml_coef(const or_sim* s, double pos, int n, double d, double* a, double* b) {
+  const double L = (double)s->pml;
+  double depth = L - pos;
+  if (pos - ((double)n - 1.0 - L) > depth) depth = pos - ((double)n - 1.0 - L);
+  if (depth < 0.0) depth = 0.0;
+  const double sig_max = 4.0 * log(1e6) / (2.0 * L * d);
+  const double r = depth / L;
+  *b = exp(-sig_max * r * r * r * s->dt);
+  *a = *b - 1.0;
 }
 
 /* S_axis applied to component array a at storage index (i,j,k). */
@@ -202,25 +251,43 @@ static double smooth(const or_sim* s, int axis, const double* a, int i, int j, i
 
 /* B += coef * curl'(E) with the smoothed curl of Sec. 2: D_i is replaced by
  * D_i S_i.  Writes into separate output arrays so that the input E is read
- * unmodified. */
-static void curl_e_add(or_sim* s, double* const E[3], double* B[3], double coef) {
+ * unmodified.  With absorbing layers the y and z derivatives carry their
+ * memory variables; update_psi = 1 first advances them with this E (the
+ * second half step of a step, whose curl the next step's first half step
+ * reuses unchanged). */
+static void curl_e_add(or_sim* s, double* const E[3], double* B[3], double coef, int update_psi) {
   const double dx = s->dx, dy = s->dy, dz = s->dz;
   for (int i = 0; i < s->nx; ++i)
     for (int j = 0; j < s->ny; ++j)
       for (int k = 0; k < s->nz; ++k) {
         size_t id = ix3(s, i, j, k);
         /* Bx at (i, j+1/2, k+1/2): D_y S_y Ez - D_z S_z Ey */
-        double cx = (smooth(s, 1, E[2], i, j + 1, k) - smooth(s, 1, E[2], i, j, k)) / dy -
-                    (smooth(s, 2, E[1], i, j, k + 1) - smooth(s, 2, E[1], i, j, k)) / dz;
+        double dyEz = (smooth(s, 1, E[2], i, j + 1, k) - smooth(s, 1, E[2], i, j, k)) / dy;
+        double dzEy = (smooth(s, 2, E[1], i, j, k + 1) - smooth(s, 2, E[1], i, j, k)) / dz;
         /* By at (i+1/2, j, k+1/2): D_z S_z Ex - D_x S_x Ez */
-        double cy = (smooth(s, 2, E[0], i, j, k + 1) - smooth(s, 2, E[0], i, j, k)) / dz -
-                    (smooth(s, 0, E[2], i + 1, j, k) - smooth(s, 0, E[2], i, j, k)) / dx;
+        double dzEx = (smooth(s, 2, E[0], i, j, k + 1) - smooth(s, 2, E[0], i, j, k)) / dz;
+        double dxEz = (smooth(s, 0, E[2], i + 1, j, k) - smooth(s, 0, E[2], i, j, k)) / dx;
         /* Bz at (i+1/2, j+1/2, k): D_x S_x Ey - D_y S_y Ex */
-        double cz = (smooth(s, 0, E[1], i + 1, j, k) - smooth(s, 0, E[1], i, j, k)) / dx -
-                    (smooth(s, 1, E[0], i, j + 1, k) - smooth(s, 1, E[0], i, j, k)) / dy;
-        B[0][id] += coef * cx;
-        B[1][id] += coef * cy;
-        B[2][id] += coef * cz;
+        double dxEy = (smooth(s, 0, E[1], i + 1, j, k) - smooth(s, 0, E[1], i, j, k)) / dx;
+        double dyEx = (smooth(s, 1, E[0], i, j + 1, k) - smooth(s, 1, E[0], i, j, k)) / dy;
+        if (s->pml) {
+          double ay, by, az, bz;
+          pml_coef(s, j + 0.5, s->ny, dy, &ay, &by);
+          pml_coef(s, k + 0.5, s->nz, dz, &az, &bz);
+          if (update_psi) {
+            s->psi[PSI_CX_Y][id] = by * s->psi[PSI_CX_Y][id] + ay * dyEz;
+            s->psi[PSI_CZ_Y][id] = by * s->psi[PSI_CZ_Y][id] + ay * dyEx;
+            s->psi[PSI_CX_Z][id] = bz * s->psi[PSI_CX_Z][id] + az * dzEy;
+            s->psi[PSI_CY_Z][id] = bz * s->psi[PSI_CY_Z][id] + az * dzEx;
+          }
+          dyEz += s->psi[PSI_CX_Y][id];
+          dyEx += s->psi[PSI_CZ_Y][id];
+          dzEy += s->psi[PSI_CX_Z][id];
+          dzEx += s->psi[PSI_CY_Z][id];
+        }
+        B[0][id] += coef * (dyEz - dzEy);
+        B[1][id] += coef * (dzEx - dxEz);
+        B[2][id] += coef * (dxEy - dyEx);
       }
 }
 
@@ -234,15 +301,28 @@ static void e_update(or_sim* s) {
     for (int j = 0; j < s->ny; ++j)
       for (int k = 0; k < s->nz; ++k) {
         size_t id = ix3(s, i, j, k);
-        double cx = (fv(s, Bz, i, j, k) - fv(s, Bz, i, j - 1, k)) / dy -
-                    (fv(s, By, i, j, k) - fv(s, By, i, j, k - 1)) / dz;
-        double cy = (fv(s, Bx, i, j, k) - fv(s, Bx, i, j, k - 1)) / dz -
-                    (fv(s, Bz, i, j, k) - fv(s, Bz, i - 1, j, k)) / dx;
-        double cz = (fv(s, By, i, j, k) - fv(s, By, i - 1, j, k)) / dx -
-                    (fv(s, Bx, i, j, k) - fv(s, Bx, i, j - 1, k)) / dy;
-        Ex[id] += dt * (cx - Jx[id]);
-        Ey[id] += dt * (cy - Jy[id]);
-        Ez[id] += dt * (cz - Jz[id]);
+        double dyBz = (fv(s, Bz, i, j, k) - fv(s, Bz, i, j - 1, k)) / dy;
+        double dzBy = (fv(s, By, i, j, k) - fv(s, By, i, j, k - 1)) / dz;
+        double dzBx = (fv(s, Bx, i, j, k) - fv(s, Bx, i, j, k - 1)) / dz;
+        double dxBz = (fv(s, Bz, i, j, k) - fv(s, Bz, i - 1, j, k)) / dx;
+        double dxBy = (fv(s, By, i, j, k) - fv(s, By, i - 1, j, k)) / dx;
+        double dyBx = (fv(s, Bx, i, j, k) - fv(s, Bx, i, j - 1, k)) / dy;
+        if (s->pml) { /* Ex at (i+1/2, j, k), Ey at (i, j+1/2, k), Ez at (i, j, k+1/2) */
+          double ay, by, az, bz;
+          pml_coef(s, (double)j, s->ny, dy, &ay, &by);
+          pml_coef(s, (double)k, s->nz, dz, &az, &bz);
+          s->psi[PSI_EX_Y][id] = by * s->psi[PSI_EX_Y][id] + ay * dyBz;
+          s->psi[PSI_EZ_Y][id] = by * s->psi[PSI_EZ_Y][id] + ay * dyBx;
+          s->psi[PSI_EX_Z][id] = bz * s->psi[PSI_EX_Z][id] + az * dzBy;
+          s->psi[PSI_EY_Z][id] = bz * s->psi[PSI_EY_Z][id] + az * dzBx;
+          dyBz += s->psi[PSI_EX_Y][id];
+          dyBx += s->psi[PSI_EZ_Y][id];
+          dzBy += s->psi[PSI_EX_Z][id];
+          dzBx += s->psi[PSI_EY_Z][id];
+        }
+        Ex[id] += dt * (dyBz - dzBy - Jx[id]);
+        Ey[id] += dt * (dzBx - dxBz - Jy[id]);
+        Ez[id] += dt * (dxBy - dyBx - Jz[id]);
       }
 }
 
@@ -250,9 +330,9 @@ static void e_update(or_sim* s) {
 void or_field_update(or_sim* s) {
   double* E[3] = {s->F[OR_EX], s->F[OR_EY], s->F[OR_EZ]};
   double* B[3] = {s->F[OR_BX], s->F[OR_BY], s->F[OR_BZ]};
-  curl_e_add(s, E, B, -0.5 * s->dt);
+  curl_e_add(s, E, B, -0.5 * s->dt, 0);
   e_update(s);
-  curl_e_add(s, E, B, -0.5 * s->dt);
+  curl_e_add(s, E, B, -0.5 * s->dt, 1);
 }
 
 /* ------------------------------------------------------------------ */
@@ -376,7 +456,7 @@ static void push_and_deposit(or_sim* s) {
     or_deposit_one(s, xi0, xi1, s->q * s->w[p]);
     for (int c = 0; c < 3; ++c) {
       double x = xi1[c];
-      if (c > 0 || s->periodic_x) {
+      if (c == 0 ? s->periodic_x : !s->pml) {
         if (x < 0.0) x += N[c];
         if (x >= N[c]) x -= N[c];
       }
@@ -453,8 +533,8 @@ static void load_cells(or_sim* s, int lo, int hi) {
   size_t first = s->np;
   for (int ci = lo; ci <= hi; ++ci) {
     long long L = s->shifts + ci;
-    for (int j = 0; j < s->ny; ++j)
-      for (int k = 0; k < s->nz; ++k) {
+    for (int j = s->pml; j < s->ny - s->pml; ++j)
+      for (int k = s->pml; k < s->nz - s->pml; ++k) {
         uint64_t cell = ((uint64_t)L * (uint64_t)s->ny + (uint64_t)j) * (uint64_t)s->nz + (uint64_t)k;
         for (int sl = 0; sl < s->ppc; ++sl) {
           uint64_t ctr = (cell * (uint64_t)s->ppc + (uint64_t)sl) * 3u;
@@ -494,13 +574,23 @@ static void load_cells(or_sim* s, int lo, int hi) {
 static int x_lo(const or_sim* s) { return s->periodic_x ? 0 : 2; }
 static int x_hi(const or_sim* s) { return s->periodic_x ? s->nx - 1 : s->nx - 4; }
 
+/* With absorbing layers, particles live in the y, z cells [L, n - L) and are
+ * absorbed when they leave them; the cubic shapes of such a particle stay
+ * inside the grid during a step for L >= 3. */
+static int inside_yz(const or_sim* s, size_t p) {
+  if (!s->pml) return 1;
+  int cy = (int)floor(s->xi[1][p]), cz = (int)floor(s->xi[2][p]);
+  return cy >= s->pml && cy < s->ny - s->pml && cz >= s->pml && cz < s->nz - s->pml;
+}
+
 static void drop_outside(or_sim* s) {
-  if (s->periodic_x) return;
+  if (s->periodic_x && !s->pml) return;
   size_t q = 0;
   int lo = x_lo(s), hi = x_hi(s);
   for (size_t p = 0; p < s->np; ++p) {
     int c = (int)floor(s->xi[0][p]);
-    if (c < lo || c > hi) continue;
+    if (!s->periodic_x && (c < lo || c > hi)) continue;
+    if (!inside_yz(s, p)) continue;
     if (q != p) {
       for (int d = 0; d < 3; ++d) {
         s->xi[d][q] = s->xi[d][p];
@@ -526,6 +616,10 @@ static void shift_window(or_sim* s) {
   }
   memmove(s->rho_ion, s->rho_ion + slab, (n - slab) * sizeof(double));
   memset(s->rho_ion + (n - slab), 0, slab * sizeof(double));
+  for (int c = 0; c < 8 && s->pml; ++c) {
+    memmove(s->psi[c], s->psi[c] + slab, (n - slab) * sizeof(double));
+    memset(s->psi[c] + (n - slab), 0, slab * sizeof(double));
+  }
   for (size_t p = 0; p < s->np; ++p) s->xi[0][p] -= 1.0;
   s->shifts += 1;
   drop_outside(s);
@@ -590,7 +684,7 @@ static void laser_in_box(or_sim* s) {
         bx -= s->dx * (fv(s, B[2], i, j, k + 1) - fv(s, B[2], i, j, k)) / s->dz;
       }
     }
-  curl_e_add(s, E, B, 0.5 * s->dt);
+  curl_e_add(s, E, B, 0.5 * s->dt, 0);
   for (int c = 0; c < 3; ++c)
     for (size_t q = 0; q < n; ++q) {
       s->F[OR_EX + c][q] += E[c][q];
@@ -608,6 +702,8 @@ or_sim* or_create(const or_grid* g, double dt_si, const or_window* w) {
   if (g->dx > g->dy || g->dx > g->dz) return NULL; /* Sec. 2 constraint */
   if (!g->periodic_x && g->nx < 8) return NULL;
   if (w && g->periodic_x) return NULL;
+  if (g->pml < 0 || (g->pml > 0 && (g->pml < 3 || g->ny < 2 * g->pml + 4 || g->nz < 2 * g->pml + 4)))
+    return NULL;
   or_sim* s = (or_sim*)calloc(1, sizeof(or_sim));
   s->nx = g->nx;
   s->ny = g->ny;
@@ -644,6 +740,8 @@ or_sim* or_create(const or_grid* g, double dt_si, const or_window* w) {
   size_t n = (size_t)s->nx * s->ny * s->nz;
   for (int c = 0; c < OR_NCOMP; ++c) s->F[c] = (double*)calloc(n, sizeof(double));
   s->rho_ion = (double*)calloc(n, sizeof(double));
+  s->pml = g->pml;
+  for (int c = 0; c < 8 && s->pml; ++c) s->psi[c] = (double*)calloc(n, sizeof(double));
   if (w) {
     s->has_window = 1;
     s->win_v = w->v;
@@ -656,6 +754,7 @@ void or_destroy(or_sim* s) {
   if (!s) return;
   for (int c = 0; c < OR_NCOMP; ++c) free(s->F[c]);
   free(s->rho_ion);
+  for (int c = 0; c < 8; ++c) free(s->psi[c]);
   for (int c = 0; c < 3; ++c) {
     free(s->xi[c]);
     free(s->u[c]);
@@ -714,12 +813,12 @@ static void step_once(or_sim* s) {
   push_and_deposit(s);
   /* Eq. (perfDispMaxwell); the boundary source imposes E_y^{n+1} on the
    * i = 0 plane after the E update and before the second B half step. */
-  curl_e_add(s, E, B, -0.5 * s->dt);
+  curl_e_add(s, E, B, -0.5 * s->dt, 0);
   e_update(s);
   s->step += 1;
   double t_new = (double)s->step * s->dt;
   if (s->laser_mode == OR_LASER_HARD_SOURCE) hard_source(s);
-  curl_e_add(s, E, B, -0.5 * s->dt);
+  curl_e_add(s, E, B, -0.5 * s->dt, 1);
   if (s->has_window && t_new > s->win_t0) {
     double tb = t_old > s->win_t0 ? t_old : s->win_t0;
     s->win_frac += s->win_v * (t_old >= s->win_t0 ? s->dt : (t_new - tb)) / s->dx;
@@ -770,6 +869,8 @@ int or_set_particles(or_sim* s, size_t n, const double* const* xi3, const double
       if (c == 0 && !s->periodic_x) {
         int cl = (int)floor(x);
         if (cl < x_lo(s) || cl > x_hi(s)) return -1;
+      } else if (c > 0 && s->pml) {
+        if (!(x >= s->pml && x < N[c] - s->pml)) return -1;
       } else if (!(x >= 0.0 && x < N[c])) {
         return -1;
       }

@@ -46,6 +46,8 @@ typedef struct {
   int periodic_x;           /* 1: periodic x, 0: open x (y, z periodic)     */
   uint64_t seed;            /* particle-loading seed                        */
   int solver;               /* 0: perfect dispersion (Sec. 2), 1: Yee      */
+  int pml;                  /* 0: y, z periodic; L > 0: L-cell absorbing    */
+                            /* layers (PML, Sec. 3.1) at both y and z ends  */
 } or_grid;
 
 typedef struct {
