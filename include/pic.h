@@ -90,7 +90,7 @@ typedef struct pic_alloc {
 } pic_alloc;
 
 typedef struct pic_grid {
-  int nx, ny, nz;       /* cells of the window along x, y, z (y, z periodic)   */
+  int nx, ny, nz;       /* cells of the window along x, y, z                   */
   double dx, dy, dz;    /* metres; dx <= dy and dx <= dz (Sec. 2 constraint)   */
   double lambda0;       /* metres; reference wavelength: omega0 and n_c        */
   double x0;            /* metres; lab-frame x of node 0 at t = 0              */
@@ -105,6 +105,18 @@ typedef struct pic_grid {
   uint32_t flags;       /* PIC_FLAG_*                                          */
   int64_t max_particles;/* particle capacity; <= 0 selects ppc * cells         */
   const pic_alloc* alloc; /* NULL: cudaMalloc / cudaFree                       */
+  int pml;              /* transverse boundaries.  0: y and z periodic.  L > 0:
+                           the outer L cells at each y and each z end are a
+                           perfectly matched absorbing layer (Sec. 3.1 uses
+                           16), fields are zero beyond the grid, plasma is
+                           loaded only in cells [L, n - L) and particles that
+                           leave them are absorbed.  Needs L >= 3 and
+                           ny, nz >= 2 L + 4.  Reading (the paper gives no
+                           form): a convolutional PML, kappa = 1, no frequency
+                           shift, sigma = sigma_max (depth / L)^3 with
+                           sigma_max = 2 ln(1e6) / (L d), stretching the y and
+                           z derivatives of both curls (the smoothed ones of
+                           the perfect-dispersion curl included).             */
 } pic_grid;
 
 typedef struct pic_window {
@@ -213,8 +225,9 @@ int pic_set_field(pic_t* h, int comp, const double* host_in);
 /* Particle access.  get: p->n is the capacity of the host arrays on entry and
  * the number of live particles on return (PIC_ERR_CAPACITY if too small; the
  * count is still returned).  set: replaces all particles; positions must lie
- * in the allowed x range (cells 2 .. nx-4 for open x) and in [0, n) for
- * periodic axes (PIC_ERR_ARG otherwise). */
+ * in the allowed x range (cells 2 .. nx-4 for open x), in [0, n) for
+ * periodic axes and in [L, n - L) for y and z with absorbing layers of L
+ * cells (PIC_ERR_ARG otherwise). */
 int pic_get_particles(pic_t* h, pic_particles* p);
 int pic_set_particles(pic_t* h, const pic_particles* p);
 

@@ -252,10 +252,11 @@ static double smooth(const or_sim* s, int axis, const double* a, int i, int j, i
 /* B += coef * curl'(E) with the smoothed curl of Sec. 2: D_i is replaced by
  * D_i S_i.  Writes into separate output arrays so that the input E is read
  * unmodified.  With absorbing layers the y and z derivatives carry their
- * memory variables; update_psi = 1 first advances them with this E (the
- * second half step of a step, whose curl the next step's first half step
- * reuses unchanged). */
-static void curl_e_add(or_sim* s, double* const E[3], double* B[3], double coef, int update_psi) {
+ * memory variables: psi_mode 2 first advances them with this E (the second
+ * half step of a step, whose curl the next step's first half step reuses
+ * with the variables as stored: psi_mode 1); psi_mode 0 leaves them out (the
+ * curl of a field increment with no history, as at the laser's set-up). */
+static void curl_e_add(or_sim* s, double* const E[3], double* B[3], double coef, int psi_mode) {
   const double dx = s->dx, dy = s->dy, dz = s->dz;
   for (int i = 0; i < s->nx; ++i)
     for (int j = 0; j < s->ny; ++j)
@@ -270,11 +271,11 @@ static void curl_e_add(or_sim* s, double* const E[3], double* B[3], double coef,
         /* Bz at (i+1/2, j+1/2, k): D_x S_x Ey - D_y S_y Ex */
         double dxEy = (smooth(s, 0, E[1], i + 1, j, k) - smooth(s, 0, E[1], i, j, k)) / dx;
         double dyEx = (smooth(s, 1, E[0], i, j + 1, k) - smooth(s, 1, E[0], i, j, k)) / dy;
-        if (s->pml) {
+        if (s->pml && psi_mode) {
           double ay, by, az, bz;
           pml_coef(s, j + 0.5, s->ny, dy, &ay, &by);
           pml_coef(s, k + 0.5, s->nz, dz, &az, &bz);
-          if (update_psi) {
+          if (psi_mode == 2) {
             s->psi[PSI_CX_Y][id] = by * s->psi[PSI_CX_Y][id] + ay * dyEz;
             s->psi[PSI_CZ_Y][id] = by * s->psi[PSI_CZ_Y][id] + ay * dyEx;
             s->psi[PSI_CX_Z][id] = bz * s->psi[PSI_CX_Z][id] + az * dzEy;
@@ -330,9 +331,9 @@ static void e_update(or_sim* s) {
 void or_field_update(or_sim* s) {
   double* E[3] = {s->F[OR_EX], s->F[OR_EY], s->F[OR_EZ]};
   double* B[3] = {s->F[OR_BX], s->F[OR_BY], s->F[OR_BZ]};
-  curl_e_add(s, E, B, -0.5 * s->dt, 0);
-  e_update(s);
   curl_e_add(s, E, B, -0.5 * s->dt, 1);
+  e_update(s);
+  curl_e_add(s, E, B, -0.5 * s->dt, 2);
 }
 
 /* ------------------------------------------------------------------ */
@@ -813,12 +814,12 @@ static void step_once(or_sim* s) {
   push_and_deposit(s);
   /* Eq. (perfDispMaxwell); the boundary source imposes E_y^{n+1} on the
    * i = 0 plane after the E update and before the second B half step. */
-  curl_e_add(s, E, B, -0.5 * s->dt, 0);
+  curl_e_add(s, E, B, -0.5 * s->dt, 1);
   e_update(s);
   s->step += 1;
   double t_new = (double)s->step * s->dt;
   if (s->laser_mode == OR_LASER_HARD_SOURCE) hard_source(s);
-  curl_e_add(s, E, B, -0.5 * s->dt, 1);
+  curl_e_add(s, E, B, -0.5 * s->dt, 2);
   if (s->has_window && t_new > s->win_t0) {
     double tb = t_old > s->win_t0 ? t_old : s->win_t0;
     s->win_frac += s->win_v * (t_old >= s->win_t0 ? s->dt : (t_new - tb)) / s->dx;

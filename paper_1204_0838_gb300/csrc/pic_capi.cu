@@ -125,7 +125,51 @@ Geom<T> geom(const pic_t* h) {
   g.dz = (T)h->dz;
   g.dyn = nullptr;
   g.gate = 0;
+  g.pml = h->pml;
   return g;
+}
+
+// Memory variables and coefficients of the absorbing layers (L = 0: none).
+template <typename T>
+Pml<T> pml_view(const pic_t* h) {
+  Pml<T> pm;
+  pm.L = h->pml;
+  pm.rows = 2 * h->pml + 1;
+  T* base = (T*)h->psi;
+  const size_t ny_ = (size_t)h->nx * pm.rows * h->nz, nz_ = (size_t)h->nx * h->ny * pm.rows;
+  for (int c = 0; c < 4; ++c) {
+    pm.py[c] = base ? base + c * ny_ : nullptr;
+    pm.pz[c] = base ? base + 4 * ny_ + c * nz_ : nullptr;
+  }
+  pm.cy = (const T*)h->pml_coef;
+  pm.cz = h->pml_coef ? (const T*)h->pml_coef + 4 * h->ny : nullptr;
+  if (!base) pm.L = 0;
+  return pm;
+}
+
+size_t psi_values(const pic_t* h) {
+  if (!h->pml) return 0;
+  const size_t rows = 2 * (size_t)h->pml + 1;
+  return 4 * ((size_t)h->nx * rows * h->nz + (size_t)h->nx * h->ny * rows);
+}
+
+// Coefficients of the convolutional layer (kappa = 1, no frequency shift):
+// sigma = sigma_max (depth / L)^3, sigma_max = 4 ln(1e6) / (2 L d) (a
+// continuous layer reflects 1e-6 at normal incidence), b = exp(-sigma dt),
+// a = b - 1.  Depth in cells at position pos (nodes integer, half nodes
+// + 1/2) of an axis of n cells: max(L - pos, pos - (n - 1 - L), 0).
+void pml_coefficients(const pic_t* h, int n, double d, double* out /* [4][n] */) {
+  const double L = h->pml;
+  const double sig_max = 4.0 * std::log(1e6) / (2.0 * L * d);
+  for (int j = 0; j < n; ++j)
+    for (int half = 0; half < 2; ++half) {
+      const double pos = j + 0.5 * half;
+      const double depth = std::max(std::max(L - pos, pos - (n - 1.0 - L)), 0.0);
+      const double r = depth / L;
+      const double b = std::exp(-sig_max * r * r * r * h->dt);
+      out[(2 * half) * n + j] = b - 1.0;
+      out[(2 * half + 1) * n + j] = b;
+    }
 }
 
 template <typename T>
@@ -261,8 +305,8 @@ Laser laser_params(const pic_t* h) {
 int x_lo(const pic_t* h) { return h->periodic_x ? 0 : 2; }
 int x_hi(const pic_t* h) { return h->periodic_x ? h->nx - 1 : h->nx - 4; }
 
-template <typename T>
-int load_cells(pic_t* h, int lo, int hi) {
+// Loading parameters for window-relative x cells [lo, hi].
+LoadSpec load_spec(const pic_t* h, int lo, int hi) {
   LoadSpec L;
   L.shifts = h->shifts;
   L.lo = lo;
@@ -278,6 +322,13 @@ int load_cells(pic_t* h, int lo, int hi) {
   L.pn = h->d_prof + h->nprof;
   L.np = h->nprof;
   L.capacity = (int)h->capacity;
+  L.pml = h->pml;
+  return L;
+}
+
+template <typename T>
+int load_cells(pic_t* h, int lo, int hi) {
+  const LoadSpec L = load_spec(h, lo, hi);
   const long long nslot = (long long)(hi - lo + 1) * h->ny * h->nz * h->ppc;
   GroupTimer tm(h, G_PART);
   k_load<T><<<grid_for(nslot, 256, 152 * 64), 256, 0, h->stream>>>(geom<T>(h), parts<T>(h, h->cur),
@@ -365,7 +416,7 @@ template <typename T>
 void launch_curl(const pic_t* h, const Geom<T>& g, int mode, int i0, int ni, cudaStream_t s) {
   const dim3 grid((ni + CB_X - 1) / CB_X, (h->ny + CB_Y - 1) / CB_Y, (h->nz + CB_Z - 1) / CB_Z);
   k_curl_tiled<T><<<grid, 256, curl_tiled_smem_bytes<T>(), s>>>(g, smooth<T>(h), fields<T>(h), curl_view<T>(h),
-                                                               field_coef<T>(h), mode, i0, ni);
+                                                               field_coef<T>(h), mode, i0, ni, pml_view<T>(h));
 }
 
 // C = curl'(E) over window-relative slabs [i0, i0 + ni).
@@ -399,25 +450,6 @@ int resort_all(pic_t* h) {
   return PIC_OK;
 }
 
-LoadSpec load_spec(const pic_t* h, int lo, int hi) {
-  LoadSpec L;
-  L.shifts = h->shifts;
-  L.lo = lo;
-  L.hi = hi;
-  L.ppc = h->ppc;
-  L.lattice = h->loading == PIC_LOAD_LATTICE;
-  for (int d = 0; d < 3; ++d) L.ns[d] = h->lat[d];
-  L.seed = h->seed;
-  L.x0 = h->x0;
-  L.dx = h->dx;
-  L.dVppc = h->dx * h->dy * h->dz / h->ppc;
-  L.px = h->d_prof;
-  L.pn = h->d_prof + h->nprof;
-  L.np = h->nprof;
-  L.capacity = (int)h->capacity;
-  return L;
-}
-
 // Window decision for the step that ends at t_new: returns 1 if the window
 // moves one cell at the end of this step (v <= c and c dt <= dx: at most one).
 int window_due(pic_t* h, double t_old, double t_new, double* frac_new) {
@@ -433,6 +465,12 @@ int zero_front_slab(pic_t* h, int storage_slab) {
   const size_t slab = (size_t)h->ny * h->nz;
   for (int c = 0; c < NCOMP; ++c)
     CK(h, cudaMemsetAsync(f.c[c] + (size_t)storage_slab * slab, 0, slab * sizeof(T), h->stream));
+  const Pml<T> pm = pml_view<T>(h);
+  for (int c = 0; c < 4 && pm.L; ++c) {
+    const size_t ny_ = (size_t)pm.rows * h->nz, nz_ = (size_t)h->ny * pm.rows;
+    CK(h, cudaMemsetAsync(pm.py[c] + (size_t)storage_slab * ny_, 0, ny_ * sizeof(T), h->stream));
+    CK(h, cudaMemsetAsync(pm.pz[c] + (size_t)storage_slab * nz_, 0, nz_ * sizeof(T), h->stream));
+  }
   return PIC_OK;
 }
 
@@ -446,7 +484,7 @@ int field_first_half(pic_t* h) {
   GroupTimer tm(h, G_FIELD);
   counted(h, G_FIELD);
   k_e_update<T><<<grid_for(h->ncell), 256, 0, h->stream>>>(geom<T>(h), fields<T>(h), curl_view<T>(h),
-                                                           field_coef<T>(h));
+                                                           field_coef<T>(h), pml_view<T>(h));
   CK(h, cudaGetLastError());
   return PIC_OK;
 }
@@ -762,6 +800,9 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
   if (g->solver != PIC_SOLVER_PERFECT && g->solver != PIC_SOLVER_YEE) return PIC_ERR_ARG;
   if (w && g->bc_x != PIC_BC_OPEN) return PIC_ERR_ARG;
   if (g->alloc && (!g->alloc->alloc || !g->alloc->free)) return PIC_ERR_ARG;
+  // absorbing layers: room for the particles' cubic stencils inside the grid
+  if (g->pml < 0 || (g->pml > 0 && (g->pml < 3 || g->ny < 2 * g->pml + 4 || g->nz < 2 * g->pml + 4)))
+    return PIC_ERR_ARG;
   pic_t* h = new (std::nothrow) pic_t();
   if (!h) return PIC_ERR_OOM;
   h->precision = g->precision;
@@ -781,6 +822,7 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
   h->flags = g->flags;
   h->max_particles = g->max_particles;
   h->solver = g->solver;
+  h->pml = g->pml;
   if (h->solver == PIC_SOLVER_YEE) {
     const double lim = 1.0 / std::sqrt(1.0 / (h->dx * h->dx) + 1.0 / (h->dy * h->dy) + 1.0 / (h->dz * h->dz));
     h->dt = dt > 0 ? dt * h->omega0 : 0.999 * lim;
@@ -810,7 +852,7 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
   }
   {
     const char* kern = std::getenv("PIC_KERNEL");
-    h->tiled = !(kern && std::strcmp(kern, "simple") == 0);
+    h->tiled = !(kern && std::strcmp(kern, "simple") == 0) || h->pml > 0;  // the simple path has no layers
     int t3[3] = {8, 8, 8};
     const char* ts = std::getenv("PIC_TILE");
     if (ts) std::sscanf(ts, "%d,%d,%d", &t3[0], &t3[1], &t3[2]);
@@ -874,6 +916,27 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
   if (!h->fields || !h->d_ctrl) {
     pic_destroy(h);
     return PIC_ERR_OOM;
+  }
+  if (h->pml) {
+    h->psi = dalloc(h, psi_values(h) * esize(h));
+    h->pml_coef = dalloc(h, 4 * (size_t)(h->ny + h->nz) * esize(h));
+    if (!h->psi || !h->pml_coef) {
+      pic_destroy(h);
+      return PIC_ERR_OOM;
+    }
+    std::vector<double> c(4 * (size_t)(h->ny + h->nz));
+    pml_coefficients(h, h->ny, h->dy, c.data());
+    pml_coefficients(h, h->nz, h->dz, c.data() + 4 * h->ny);
+    std::vector<float> cf(c.begin(), c.end());
+    const void* src = h->precision == PIC_FP64 ? (const void*)c.data() : (const void*)cf.data();
+    cudaError_t e = cudaMemcpyAsync(h->pml_coef, src, c.size() * esize(h), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->psi, 0, psi_values(h) * esize(h), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // the host copies die here
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      pic_destroy(h);
+      return PIC_ERR_CUDA;
+    }
   }
   if (cudaMemsetAsync(h->fields, 0, NCOMP * h->ncell * esize(h), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->tstart[0], 0, sizeof(int) * (h->tiles.n + 1), h->stream) != cudaSuccess ||
@@ -1101,6 +1164,8 @@ int pic_set_particles(pic_t* h, const pic_particles* p) {
       if (d == 0 && !h->periodic_x) {
         const double c = std::floor(x);
         if (!(c >= x_lo(h) && c <= x_hi(h))) return fail(h, PIC_ERR_ARG, "particle outside the allowed x range");
+      } else if (d > 0 && h->pml) {
+        if (!(x >= h->pml && x < N[d] - h->pml)) return fail(h, PIC_ERR_ARG, "particle inside an absorbing layer");
       } else if (!(x >= 0.0 && x < N[d])) {
         return fail(h, PIC_ERR_ARG, "particle outside the box");
       }
@@ -1174,10 +1239,52 @@ int pic_set_particles(pic_t* h, const pic_particles* p) {
 namespace {
 struct CkptHeader {
   char magic[8];  // "PICCKPT1"
-  int version, precision, nx, ny, nz, ppc, has_ids, pad;
+  int version, precision, nx, ny, nz, ppc, has_ids, pml;
   long long step, shifts, np, pushed;
   double win_frac;
 };
+
+// Memory variables of the absorbing layers in window-relative slab order, as
+// doubles (to_host) or back into the storage slabs (from host).
+int psi_io(pic_t* h, std::vector<double>& host, bool to_host) {
+  const size_t n = psi_values(h);
+  if (!n) return PIC_OK;
+  const size_t es = esize(h);
+  std::vector<unsigned char> raw(n * es);
+  if (to_host) {
+    CK(h, cudaMemcpyAsync(raw.data(), h->psi, raw.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    host.assign(n, 0.0);
+  } else if (host.size() != n) {
+    return fail(h, PIC_ERR_STATE, "absorbing-layer state of the wrong size");
+  }
+  const size_t rows = 2 * (size_t)h->pml + 1;
+  const size_t per_slab[2] = {rows * h->nz, (size_t)h->ny * rows};  // y arrays, z arrays
+  size_t off = 0;
+  for (int c = 0; c < 8; ++c) {
+    const size_t ps = per_slab[c / 4];
+    for (int i = 0; i < h->nx; ++i) {
+      const size_t st = off + (size_t)((i + h->origin) % h->nx) * ps, wr = off + (size_t)i * ps;
+      for (size_t q = 0; q < ps; ++q) {
+        double* hv = &host[wr + q];
+        unsigned char* rv = &raw[(st + q) * es];
+        if (to_host) {
+          if (es == 8) std::memcpy(hv, rv, 8);
+          else { float v; std::memcpy(&v, rv, 4); *hv = v; }
+        } else {
+          if (es == 8) std::memcpy(rv, hv, 8);
+          else { const float v = (float)*hv; std::memcpy(rv, &v, 4); }
+        }
+      }
+    }
+    off += ps * h->nx;
+  }
+  if (!to_host) {
+    CK(h, cudaMemcpyAsync(h->psi, raw.data(), raw.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+  }
+  return PIC_OK;
+}
 }  // namespace
 
 int pic_save(pic_t* h, const char* path) {
@@ -1195,6 +1302,7 @@ int pic_save(pic_t* h, const char* path) {
   hd.nz = h->nz;
   hd.ppc = h->ppc;
   hd.has_ids = h->pb[0].id != nullptr;
+  hd.pml = h->pml;
   hd.step = h->step;
   hd.shifts = h->shifts;
   hd.np = h->capacity > 0 ? h->np_host : 0;
@@ -1223,6 +1331,11 @@ int pic_save(pic_t* h, const char* path) {
     ok = rc == PIC_OK && std::fwrite(a.data(), sizeof(double), a.size(), f) == a.size();
     if (ok && hd.has_ids) ok = std::fwrite(ids.data(), sizeof(uint32_t), ids.size(), f) == ids.size();
   }
+  if (ok && h->pml) {
+    std::vector<double> ps;
+    rc = psi_io(h, ps, true);
+    ok = rc == PIC_OK && std::fwrite(ps.data(), sizeof(double), ps.size(), f) == ps.size();
+  }
   if (std::fclose(f) != 0) ok = false;
   if (!ok) return rc ? rc : fail(h, PIC_ERR_ARG, "writing the checkpoint failed");
   return PIC_OK;
@@ -1238,9 +1351,10 @@ int pic_load(pic_t* h, const char* path) {
     std::fclose(f);
     return fail(h, PIC_ERR_STATE, "not a checkpoint of this library");
   }
-  if (hd.precision != h->precision || hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz || hd.ppc != h->ppc) {
+  if (hd.precision != h->precision || hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz || hd.ppc != h->ppc ||
+      hd.pml != h->pml) {
     std::fclose(f);
-    return fail(h, PIC_ERR_ARG, "checkpoint grid, precision or ppc differ from the handle");
+    return fail(h, PIC_ERR_ARG, "checkpoint grid, precision, ppc or absorbing layers differ from the handle");
   }
   std::vector<double> buf(h->ncell);
   int rc = PIC_OK;
@@ -1265,6 +1379,13 @@ int pic_load(pic_t* h, const char* path) {
       pp.id = hd.has_ids ? ids.data() : nullptr;
       rc = pic_set_particles(h, &pp);
     }
+  }
+  if (rc == PIC_OK && h->pml) {
+    std::vector<double> ps(psi_values(h));
+    if (std::fread(ps.data(), sizeof(double), ps.size(), f) != ps.size())
+      rc = fail(h, PIC_ERR_STATE, "truncated checkpoint");
+    else
+      rc = psi_io(h, ps, false);
   }
   std::fclose(f);
   if (rc) return rc;
@@ -1375,6 +1496,7 @@ int set_tiles(pic_t* h, int tx, int ty, int tz) {
 struct Snapshot {
   void* fields = nullptr;
   void* curl = nullptr;
+  void* psi = nullptr;  // absorbing-layer memory variables (none without layers)
   void* part = nullptr;
   int ctrl[6];
   int cur = 0;
@@ -1397,6 +1519,11 @@ int snapshot_take(pic_t* h, Snapshot* sn) {
   if (!sn->fields || !sn->curl || !sn->part) return fail(h, PIC_ERR_OOM, "autotune snapshot");
   CK(h, cudaMemcpyAsync(sn->fields, h->fields, NCOMP * h->ncell * es, cudaMemcpyDeviceToDevice, h->stream));
   CK(h, cudaMemcpyAsync(sn->curl, h->curl, 3 * h->ncell * es, cudaMemcpyDeviceToDevice, h->stream));
+  if (h->psi) {
+    sn->psi = dalloc(h, psi_values(h) * es);
+    if (!sn->psi) return fail(h, PIC_ERR_OOM, "autotune snapshot");
+    CK(h, cudaMemcpyAsync(sn->psi, h->psi, psi_values(h) * es, cudaMemcpyDeviceToDevice, h->stream));
+  }
   const PartBuf& b = h->pb[h->cur];
   char* dst = (char*)sn->part;
   const size_t n = sn->np;
@@ -1424,6 +1551,7 @@ int snapshot_restore(pic_t* h, Snapshot* sn) {
   CK(h, cudaStreamSynchronize(h->stream));
   CK(h, cudaMemcpyAsync(h->fields, sn->fields, NCOMP * h->ncell * es, cudaMemcpyDeviceToDevice, h->stream));
   CK(h, cudaMemcpyAsync(h->curl, sn->curl, 3 * h->ncell * es, cudaMemcpyDeviceToDevice, h->stream));
+  if (sn->psi) CK(h, cudaMemcpyAsync(h->psi, sn->psi, psi_values(h) * es, cudaMemcpyDeviceToDevice, h->stream));
   const PartBuf& b = h->pb[0];
   const char* src = (const char*)sn->part;
   const size_t n = sn->np;
@@ -1449,14 +1577,15 @@ int snapshot_restore(pic_t* h, Snapshot* sn) {
   CK(h, cudaStreamSynchronize(h->stream));
   dfree(h, sn->fields);
   dfree(h, sn->curl);
+  dfree(h, sn->psi);
   dfree(h, sn->part);
   return PIC_OK;
 }
 
 std::string tune_key(const pic_t* h) {
   char buf[128];
-  std::snprintf(buf, sizeof(buf), "%s:ppc%d:%dx%dx%d", h->precision == PIC_FP64 ? "fp64" : "fp32", h->ppc, h->nx,
-                h->ny, h->nz);
+  std::snprintf(buf, sizeof(buf), "%s:ppc%d:%dx%dx%d%s", h->precision == PIC_FP64 ? "fp64" : "fp32", h->ppc, h->nx,
+                h->ny, h->nz, h->pml ? ":pml" : "");
   return buf;
 }
 
@@ -1644,10 +1773,10 @@ int enqueue_step_dyn(pic_t* h, cudaStream_t s, int cur, long long* kernels) {
   k_push_tiled<T><<<tl.n, 256, tiled_smem_bytes<T>(tl), s>>>(g, tl, f, parts<T>(h, cur), h->tstart[cur],
                                                             (int)h->capacity, h->keys, h->tcnt, hq, (T)h->q, 0,
                                                             x_lo(h), x_hi(h), h->d_pushed, h->d_ctrl + 2);
-  k_e_update<T><<<grid_for(n), 256, 0, s>>>(g, f, curl_view<T>(h), fc);
+  k_e_update<T><<<grid_for(n), 256, 0, s>>>(g, f, curl_view<T>(h), fc, pml_view<T>(h));
   launch_curl<T>(h, g, 1, 0, h->nx, s);
   k_window_commit<<<1, 32, 0, s>>>(h->d_dyn);
-  k_zero_front_slab<T><<<grid_for((long long)NCOMP * h->ny * h->nz), 256, 0, s>>>(gs, f);
+  k_zero_front_slab<T><<<grid_for((long long)NCOMP * h->ny * h->nz), 256, 0, s>>>(gs, f, pml_view<T>(h));
   launch_curl<T>(h, gs, 0, 0, 1, s);
   launch_curl<T>(h, gs, 0, h->nx - 1, 1, s);
   (void)S;

@@ -37,7 +37,31 @@ struct Geom {
   T dt, dx, dy, dz;
   const DynState* dyn;  // non-null: origin (and shift) come from the device
   int gate;             // with dyn: 1 = the kernel runs only on a shift step
+  int pml;              // 0: y, z periodic; L > 0: absorbing layers, zero beyond the grid
 };
+
+// Transverse absorbing layers (convolutional PML, Sec. 3.1).  In the outer L
+// cells of y (and of z) a y derivative dF/dy of the field update becomes
+// dF/dy + psi with psi <- b psi + a dF/dy, once per step at the derivative's
+// time level; b = exp(-sigma dt), a = b - 1 (kappa = 1, no frequency shift).
+// The memory variables live in compact arrays over the rows that can have
+// sigma > 0: y index j < L or j >= ny - 1 - L (2 L + 1 rows), likewise z.
+template <typename T>
+struct Pml {
+  int L;                 // 0: no layers (all pointers null)
+  int rows;              // 2 L + 1
+  T* py[4];              // [slab][row][nz]: d_y Bz in Ex, d_y Bx in Ez, D_y S_y Ez in Bx, D_y S_y Ex in Bz
+  T* pz[4];              // [slab][ny][row]: d_z By in Ex, d_z Bx in Ey, D_z S_z Ey in Bx, D_z S_z Ex in By
+  const T* cy;           // [4][ny]: a at node j, b at node j, a at j + 1/2, b at j + 1/2
+  const T* cz;           // [4][nz], the same for z
+};
+
+// Compact row of index j on an axis of n cells with L-cell layers, or -1.
+__device__ __forceinline__ int pml_row(int j, int n, int L) {
+  if (j < L) return j;
+  if (j >= n - 1 - L) return j - (n - 1 - L) + L;
+  return -1;
+}
 
 // Apply the device-side step state to a kernel's geometry; false means the
 // kernel has nothing to do this step.

@@ -13,8 +13,12 @@ namespace pic {
 template <typename T>
 __device__ __forceinline__ T ld(const T* __restrict__ a, const Geom<T>& g, int s, int j, int k) {
   if (s < 0) return T(0);
-  j = (j < 0) ? j + g.ny : (j >= g.ny ? j - g.ny : j);
-  k = (k < 0) ? k + g.nz : (k >= g.nz ? k - g.nz : k);
+  if (g.pml) {
+    if (j < 0 || j >= g.ny || k < 0 || k >= g.nz) return T(0);
+  } else {
+    j = (j < 0) ? j + g.ny : (j >= g.ny ? j - g.ny : j);
+    k = (k < 0) ? k + g.nz : (k >= g.nz ? k - g.nz : k);
+  }
   return a[(size_t)s * g.nyz + (size_t)j * g.nz + k];
 }
 
@@ -114,6 +118,7 @@ template <typename T>
 __device__ __forceinline__ T bhalf(const T* __restrict__ B, const T* __restrict__ C, const Geom<T>& g, int s,
                                    int j, int k, T hdt) {
   if (s < 0) return T(0);
+  if (g.pml && (j < 0 || k < 0)) return T(0);
   j = (j < 0) ? j + g.ny : j;
   k = (k < 0) ? k + g.nz : k;
   const size_t id = (size_t)s * g.nyz + (size_t)j * g.nz + k;
@@ -121,7 +126,7 @@ __device__ __forceinline__ T bhalf(const T* __restrict__ B, const T* __restrict_
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_e_update(Geom<T> g, Fields<T> f, Fields<T> cc, FieldCoef<T> fc) {
+__global__ void __launch_bounds__(256) k_e_update(Geom<T> g, Fields<T> f, Fields<T> cc, FieldCoef<T> fc, Pml<T> pm) {
   if (!dyn_prologue(g)) return;
   const int nyz = g.nyz;
   const long long ncell = (long long)g.nx * nyz;
@@ -137,12 +142,37 @@ __global__ void __launch_bounds__(256) k_e_update(Geom<T> g, Fields<T> f, Fields
     const T bx = Bx[id] - fc.hdt * Cx[id];
     const T by = By[id] - fc.hdt * Cy[id];
     const T bz = Bz[id] - fc.hdt * Cz[id];
-    const T cx = (bz - bhalf(Bz, Cz, g, s, j - 1, k, fc.hdt)) * fc.idy - (by - bhalf(By, Cy, g, s, j, k - 1, fc.hdt)) * fc.idz;
-    const T cy = (bx - bhalf(Bx, Cx, g, s, j, k - 1, fc.hdt)) * fc.idz - (bz - bhalf(Bz, Cz, g, sm, j, k, fc.hdt)) * fc.idx;
-    const T cz = (by - bhalf(By, Cy, g, sm, j, k, fc.hdt)) * fc.idx - (bx - bhalf(Bx, Cx, g, s, j - 1, k, fc.hdt)) * fc.idy;
-    f.c[EX][id] += fc.dt * (cx - f.c[JX][id]);
-    f.c[EY][id] += fc.dt * (cy - f.c[JY][id]);
-    f.c[EZ][id] += fc.dt * (cz - f.c[JZ][id]);
+    T dyBz = (bz - bhalf(Bz, Cz, g, s, j - 1, k, fc.hdt)) * fc.idy;
+    T dzBy = (by - bhalf(By, Cy, g, s, j, k - 1, fc.hdt)) * fc.idz;
+    T dzBx = (bx - bhalf(Bx, Cx, g, s, j, k - 1, fc.hdt)) * fc.idz;
+    const T dxBz = (bz - bhalf(Bz, Cz, g, sm, j, k, fc.hdt)) * fc.idx;
+    const T dxBy = (by - bhalf(By, Cy, g, sm, j, k, fc.hdt)) * fc.idx;
+    T dyBx = (bx - bhalf(Bx, Cx, g, s, j - 1, k, fc.hdt)) * fc.idy;
+    if (pm.L) {  // Ex (i+1/2, j, k), Ey (i, j+1/2, k), Ez (i, j, k+1/2): y and z at nodes
+      const int jr = pml_row(j, g.ny, pm.L);
+      if (jr >= 0) {
+        const T a = pm.cy[j], b = pm.cy[g.ny + j];
+        const size_t pi = ((size_t)s * pm.rows + jr) * g.nz + k;
+        const T p0 = b * pm.py[0][pi] + a * dyBz, p1 = b * pm.py[1][pi] + a * dyBx;
+        pm.py[0][pi] = p0;
+        pm.py[1][pi] = p1;
+        dyBz += p0;
+        dyBx += p1;
+      }
+      const int kr = pml_row(k, g.nz, pm.L);
+      if (kr >= 0) {
+        const T a = pm.cz[k], b = pm.cz[g.nz + k];
+        const size_t pi = ((size_t)s * g.ny + j) * pm.rows + kr;
+        const T p0 = b * pm.pz[0][pi] + a * dzBy, p1 = b * pm.pz[1][pi] + a * dzBx;
+        pm.pz[0][pi] = p0;
+        pm.pz[1][pi] = p1;
+        dzBy += p0;
+        dzBx += p1;
+      }
+    }
+    f.c[EX][id] += fc.dt * ((dyBz - dzBy) - f.c[JX][id]);
+    f.c[EY][id] += fc.dt * ((dzBx - dxBz) - f.c[JY][id]);
+    f.c[EZ][id] += fc.dt * ((dxBy - dyBx) - f.c[JZ][id]);
   }
 }
 
@@ -173,7 +203,7 @@ size_t curl_tiled_smem_bytes() {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_curl_tiled(Geom<T> g, Smooth<T> S, Fields<T> f, Fields<T> cc,
-                                                   FieldCoef<T> fc, int mode, int i0, int ni) {
+                                                   FieldCoef<T> fc, int mode, int i0, int ni, Pml<T> pm) {
   if (!dyn_prologue(g)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sE = reinterpret_cast<T*>(smem_raw);  // [3][CE_X][CE_Y][CE_Z], origin (bx-1, by-1, bz-1)
@@ -190,8 +220,16 @@ __global__ void __launch_bounds__(256) k_curl_tiled(Geom<T> g, Smooth<T> S, Fiel
   for (int q = tid; q < CE_N; q += blockDim.x) {
     const int lz = q % CE_Z, r = q / CE_Z;
     const int ly = r % CE_Y, lx = r / CE_Y;
-    const int s = slab_of(g, bx - 1 + lx);
-    const int j = wrapi(by - 1 + ly, g.ny), k = wrapi(bz - 1 + lz, g.nz);  // blocks may exceed small ny, nz
+    int s = slab_of(g, bx - 1 + lx);
+    int j = by - 1 + ly, k = bz - 1 + lz;
+    if (g.pml) {  // zero beyond the grid
+      if (j < 0 || j >= g.ny || k < 0 || k >= g.nz) s = -1;
+      j = min(max(j, 0), g.ny - 1);
+      k = min(max(k, 0), g.nz - 1);
+    } else {
+      j = wrapi(j, g.ny);  // blocks may exceed small ny, nz
+      k = wrapi(k, g.nz);
+    }
     const size_t gi = (size_t)(s < 0 ? 0 : s) * g.nyz + (size_t)j * g.nz + k;
 #pragma unroll
     for (int c = 0; c < 3; ++c) sE[c * CE_N + q] = s < 0 ? T(0) : f.c[EX + c][gi];
@@ -252,10 +290,44 @@ __global__ void __launch_bounds__(256) k_curl_tiled(Geom<T> g, Smooth<T> S, Fiel
     const int y0 = (lx * (CB_Y + 1) + ly) * CB_Z + lz, y1 = (lx * (CB_Y + 1) + ly + 1) * CB_Z + lz;
     const int z0 = (lx * CB_Y + ly) * (CB_Z + 1) + lz;
     // Bx: D_y S_y Ez - D_z S_z Ey; By: D_z S_z Ex - D_x S_x Ez; Bz: D_x S_x Ey - D_y S_y Ex
-    const T cx = (sSyEz[y1] - sSyEz[y0]) * fc.idy - (sSzEy[z0 + 1] - sSzEy[z0]) * fc.idz;
-    const T cy = (sSzEx[z0 + 1] - sSzEx[z0]) * fc.idz - (sSxEz[x1] - sSxEz[x0]) * fc.idx;
-    const T cz = (sSxEy[x1] - sSxEy[x0]) * fc.idx - (sSyEx[y1] - sSyEx[y0]) * fc.idy;
-    const size_t id = (size_t)slab_of(g, i) * g.nyz + (size_t)j * g.nz + k;
+    T dyEz = (sSyEz[y1] - sSyEz[y0]) * fc.idy, dzEy = (sSzEy[z0 + 1] - sSzEy[z0]) * fc.idz;
+    T dzEx = (sSzEx[z0 + 1] - sSzEx[z0]) * fc.idz;
+    const T dxEz = (sSxEz[x1] - sSxEz[x0]) * fc.idx, dxEy = (sSxEy[x1] - sSxEy[x0]) * fc.idx;
+    T dyEx = (sSyEx[y1] - sSyEx[y0]) * fc.idy;
+    const int slab = slab_of(g, i);
+    if (pm.L) {  // Bx (i, j+1/2, k+1/2), By (i+1/2, j, k+1/2), Bz (i+1/2, j+1/2, k): half nodes
+      // mode 1 advances the memory variables with E^{n+1}; mode 0 uses them as stored
+      const int jr = pml_row(j, g.ny, pm.L);
+      if (jr >= 0) {
+        const size_t pi = ((size_t)slab * pm.rows + jr) * g.nz + k;
+        T p2 = pm.py[2][pi], p3 = pm.py[3][pi];
+        if (mode == 1) {
+          const T a = pm.cy[2 * g.ny + j], b = pm.cy[3 * g.ny + j];
+          p2 = b * p2 + a * dyEz;
+          p3 = b * p3 + a * dyEx;
+          pm.py[2][pi] = p2;
+          pm.py[3][pi] = p3;
+        }
+        dyEz += p2;
+        dyEx += p3;
+      }
+      const int kr = pml_row(k, g.nz, pm.L);
+      if (kr >= 0) {
+        const size_t pi = ((size_t)slab * g.ny + j) * pm.rows + kr;
+        T p2 = pm.pz[2][pi], p3 = pm.pz[3][pi];
+        if (mode == 1) {
+          const T a = pm.cz[2 * g.nz + k], b = pm.cz[3 * g.nz + k];
+          p2 = b * p2 + a * dzEy;
+          p3 = b * p3 + a * dzEx;
+          pm.pz[2][pi] = p2;
+          pm.pz[3][pi] = p3;
+        }
+        dzEy += p2;
+        dzEx += p3;
+      }
+    }
+    const T cx = dyEz - dzEy, cy = dzEx - dxEz, cz = dxEy - dyEx;
+    const size_t id = (size_t)slab * g.nyz + (size_t)j * g.nz + k;
     if (mode == 1) {
       f.c[BX][id] = (f.c[BX][id] - fc.hdt * cc.c[0][id]) - fc.hdt * cx;
       f.c[BY][id] = (f.c[BY][id] - fc.hdt * cc.c[1][id]) - fc.hdt * cy;
@@ -495,13 +567,15 @@ __global__ void k_laser_scan(Geom<T> g, const T* Ey, T* Ex, const T* Bz, T* Bx) 
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const int j = r / g.nz, k = r - j * g.nz;
     const int jm = j == 0 ? g.ny - 1 : j - 1, kp = k + 1 == g.nz ? 0 : k + 1;
+    // with absorbing layers the neighbours beyond the grid are zero, not wrapped
+    const bool jm_in = !(g.pml && j == 0), kp_in = !(g.pml && k + 1 == g.nz);
     T ex = T(0), bx = T(0);
     for (int i = 0; i < g.nx; ++i) {
       const size_t sb = (size_t)slab_of(g, i) * n;
-      ex -= g.dx * (Ey[sb + j * g.nz + k] - Ey[sb + jm * g.nz + k]) / g.dy;
+      ex -= g.dx * (Ey[sb + j * g.nz + k] - (jm_in ? Ey[sb + jm * g.nz + k] : T(0))) / g.dy;
       Ex[sb + r] = ex;
       Bx[sb + r] = bx;
-      bx -= g.dx * (Bz[sb + j * g.nz + kp] - Bz[sb + j * g.nz + k]) / g.dz;
+      bx -= g.dx * ((kp_in ? Bz[sb + j * g.nz + kp] : T(0)) - Bz[sb + j * g.nz + k]) / g.dz;
     }
   }
 }
@@ -534,6 +608,7 @@ struct LoadSpec {
   const double* pn;
   int np;
   int capacity;
+  int pml;            // plasma only in y, z cells [pml, n - pml)
 };
 
 template <typename T>
@@ -568,7 +643,8 @@ __global__ void k_load(Geom<T> g, Parts<T> p, int* d_np, int* d_err, LoadSpec L)
         o[1] = rr[1];
         o[2] = rr[2];
       }
-      n = profile_at(L.px, L.pn, L.np, L.x0 + ((double)lab + o[0]) * L.dx);
+      const bool inner = j >= L.pml && j < g.ny - L.pml && k >= L.pml && k < g.nz - L.pml;
+      n = inner ? profile_at(L.px, L.pn, L.np, L.x0 + ((double)lab + o[0]) * L.dx) : 0.0;
       want = n > 0.0;
     }
     const int slot = warp_append(d_np, want);
@@ -797,13 +873,24 @@ static __global__ void k_window_commit(DynState* d) {
 // On a shift step: zero all components of the storage slab that left the
 // window at the back (it is the new front slab).
 template <typename T>
-__global__ void k_zero_front_slab(Geom<T> g, Fields<T> f) {
+__global__ void k_zero_front_slab(Geom<T> g, Fields<T> f, Pml<T> pm) {
   if (!dyn_prologue(g)) return;
   const int slab = (g.origin + g.nx - 1) % g.nx;
   const long long n = (long long)NCOMP * g.nyz;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(q / g.nyz), r = (int)(q - (long long)c * g.nyz);
     f.c[c][(size_t)slab * g.nyz + r] = T(0);
+  }
+  if (!pm.L) return;
+  const long long ny_ = (long long)pm.rows * g.nz, nz_ = (long long)g.ny * pm.rows;  // per slab and array
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 4 * (ny_ + nz_);
+       q += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(q / (ny_ + nz_));
+    const long long r = q - c * (ny_ + nz_);
+    if (r < ny_)
+      pm.py[c][(size_t)slab * ny_ + r] = T(0);
+    else
+      pm.pz[c][(size_t)slab * nz_ + (r - ny_)] = T(0);
   }
 }
 

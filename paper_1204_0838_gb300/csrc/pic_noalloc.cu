@@ -113,6 +113,7 @@ int diag_noalloc(pic_t* h, int kind, double* out, size_t len, const pic_diag_arg
   g.dz = (T)h->dz;
   g.dyn = nullptr;
   g.gate = 0;
+  g.pml = h->pml;
   Fields<T> f;
   for (int c = 0; c < NCOMP; ++c) f.c[c] = (T*)h->fields + (size_t)c * h->ncell;
   Parts<T> p;

@@ -42,6 +42,12 @@ struct pic_t {
   void* fields = nullptr;   // 9 component arrays of ncell values
   void* curl = nullptr;     // cached smoothed curl of E (3 arrays)
   bool curl_valid = false;  // false: recompute before the next step
+  // transverse absorbing layers (0: y, z periodic): 8 compact memory-variable
+  // arrays (4 of nx (2L+1) nz for y, 4 of nx ny (2L+1) for z) and the
+  // per-index coefficients (a, b at nodes and half nodes for y, then z)
+  int pml = 0;
+  void* psi = nullptr;
+  void* pml_coef = nullptr;
   // tile-sorted particles
   bool tiled = true;
   pic::Tiles tiles = {1, 1, 1, 1, 1, 1, 1};

@@ -290,6 +290,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom
         if (rel < 0) rel += g.nx;
         if (rel < xlo || rel > xhi) key = -1;
       }
+      // absorbing layers: a particle that leaves the y, z cells [L, n - L) is absorbed
+      if (g.pml && (n1 < g.pml || n1 >= g.ny - g.pml || n2 < g.pml || n2 >= g.nz - g.pml)) key = -1;
       keys[pi] = key;
       }
     }
@@ -425,7 +427,8 @@ __global__ void k_inject_tiled(Geom<T> g, Tiles tl, Parts<T> p, LoadSpec L, int 
         o[1] = rr[1];
         o[2] = rr[2];
       }
-      n = profile_at(L.px, L.pn, L.np, L.x0 + ((double)lab + o[0]) * L.dx);
+      const bool inner = j >= L.pml && j < g.ny - L.pml && k >= L.pml && k < g.nz - L.pml;
+      n = inner ? profile_at(L.px, L.pn, L.np, L.x0 + ((double)lab + o[0]) * L.dx) : 0.0;
       sx = slab_of(g, ci);
       if (n > 0.0) key = tile_of(g, tl, sx, j, k);
     }

@@ -41,7 +41,7 @@ class pic_grid(C.Structure):
                 ("precision", C.c_int), ("bc_x", C.c_int), ("solver", C.c_int),
                 ("seed", C.c_uint64),
                 ("flags", C.c_uint32), ("max_particles", C.c_int64),
-                ("alloc", C.POINTER(pic_alloc))]
+                ("alloc", C.POINTER(pic_alloc)), ("pml", C.c_int)]
 
 
 class pic_window(C.Structure):
@@ -370,14 +370,14 @@ class Sim:
 
     def __init__(self, nx, ny, nz, dx, dy, dz, lambda0, x0=0.0, periodic_x=True,
                  precision="fp64", seed=12040838, dt=0.0, window=None, track_ids=False,
-                 max_particles=0, use_torch=True, solver="perfect"):
+                 max_particles=0, use_torch=True, solver="perfect", pml=0):
         self._mem = TorchMemory() if use_torch else None
         g = pic_grid(nx, ny, nz, dx, dy, dz, lambda0, x0,
                      PIC_FP64 if precision == "fp64" else PIC_FP32,
                      PIC_BC_PERIODIC if periodic_x else PIC_BC_OPEN,
                      PIC_SOLVER_YEE if solver == "yee" else PIC_SOLVER_PERFECT, seed,
                      PIC_FLAG_TRACK_IDS if track_ids else 0, int(max_particles),
-                     C.pointer(self._mem.struct) if self._mem else None)
+                     C.pointer(self._mem.struct) if self._mem else None, int(pml))
         w = pic_window(window[0], window[1]) if window is not None else None
         self.h = pic_create(g, dt, w)
         self.shape = (nx, ny, nz)

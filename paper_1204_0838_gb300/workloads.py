@@ -89,16 +89,18 @@ def batch_configs(n=32, seed=DEFAULT_SEED):
 
 
 def random_state(shape, n_particles, seed, umax=2.0, periodic_x=True, field_scale=0.1,
-                 weight=0.01, dV=1.0):
+                 weight=0.01, dV=1.0, yz_margin=0):
     """Seeded random fields (9, nx, ny, nz) and particles (grid-unit positions
-    inside the allowed range, momenta in [-umax, umax], positive weights)."""
+    inside the allowed range, momenta in [-umax, umax], positive weights);
+    yz_margin keeps y and z inside [margin, n - margin) (absorbing layers)."""
     nx, ny, nz = shape
     rng = np.random.default_rng(seed)
     fields = rng.standard_normal((9, nx, ny, nz)) * field_scale
     fields[6:] = 0.0
     lo, hi = (0.0, nx) if periodic_x else (3.0, nx - 5.0)
-    xi = np.stack([rng.uniform(lo, hi, n_particles), rng.uniform(0, ny, n_particles),
-                   rng.uniform(0, nz, n_particles)])
+    m = float(yz_margin)
+    xi = np.stack([rng.uniform(lo, hi, n_particles), rng.uniform(m, ny - m, n_particles),
+                   rng.uniform(m, nz - m, n_particles)])
     u = rng.uniform(-umax, umax, (3, n_particles))
     w = rng.uniform(0.5, 1.5, n_particles) * weight * dV
     ids = np.arange(n_particles, dtype=np.uint32)

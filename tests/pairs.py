@@ -9,7 +9,7 @@ def make_gpu(cfg, track_ids=True, precision=None, laser=True, species=True, max_
     g = pic.Sim(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"], cfg["lambda0"],
                 x0=cfg["x0"], periodic_x=cfg["periodic_x"], precision=precision or cfg["precision"],
                 seed=cfg["seed"], window=cfg["window"], track_ids=track_ids,
-                max_particles=max_particles)
+                max_particles=max_particles, pml=cfg.get("pml", 0))
     if species:
         g.add_species(cfg["prof_x"], cfg["prof_n"], cfg["ppc"], loading=cfg["loading"])
     if laser:
@@ -19,7 +19,8 @@ def make_gpu(cfg, track_ids=True, precision=None, laser=True, species=True, max_
 
 def make_oracle(cfg, laser=True, species=True):
     o = O.Sim(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"], cfg["lambda0"],
-              x0=cfg["x0"], periodic_x=cfg["periodic_x"], seed=cfg["seed"], window=cfg["window"])
+              x0=cfg["x0"], periodic_x=cfg["periodic_x"], seed=cfg["seed"], window=cfg["window"],
+              pml=cfg.get("pml", 0))
     if species:
         o.add_species(cfg["prof_x"], cfg["prof_n"], cfg["ppc"], loading=cfg["loading"])
     if laser:

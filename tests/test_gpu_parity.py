@@ -368,3 +368,98 @@ def test_checkpoint_resume_continues_the_run(tmp_path):
     with pytest.raises(pic.PicError):  # a different grid is refused
         c = pic.Sim(32, 8, 8, LAM / 8, LAM / 4, LAM / 2, LAM)
         pic.pic_load(c.h, path)
+
+
+# ---------------------------------------------------------------------------
+# transverse absorbing layers (Sec. 3.1: a PML surrounds the box transversely)
+# ---------------------------------------------------------------------------
+def _pml_pair(shape, L, periodic, solver="perfect", precision="fp64", dx=LAM / 8, dy=LAM / 4, dz=LAM / 4):
+    g = pic.Sim(*shape, dx, dy, dz, LAM, periodic_x=periodic, precision=precision, track_ids=True,
+                solver=solver, pml=L)
+    o = O.Sim(*shape, dx, dy, dz, LAM, periodic_x=periodic, solver=solver, pml=L)
+    return g, o
+
+
+@pytest.mark.parametrize("solver", ["perfect", "yee"])
+def test_pml_field_parity(solver):
+    shape, L = (24, 40, 36), 8  # z spans a full and a ragged 32-cell curl block
+    g, o = _pml_pair(shape, L, True, solver)
+    rng = np.random.default_rng(21)
+    F = rng.standard_normal((9,) + shape) * 0.1
+    F[6:] = 0.0
+    for s in (g, o):
+        s.set_fields(F)
+    g.step(1)
+    o.step(1)
+    compare_fields(g, o, 1e-12)
+    g.step(29)  # the memory variables of every layer cell are active by now
+    o.step(29)
+    compare_fields(g, o, 1e-10)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_pml_particles_push_deposit_and_absorption(periodic):
+    shape, L = (40, 28, 28), 6
+    g, o = _pml_pair(shape, L, periodic)
+    inf = o.info()
+    F, xi, u, w, ids = W.random_state(shape, 20000, 22, umax=3.0, periodic_x=periodic,
+                                      dV=inf["dx"] * inf["dy"] * inf["dz"], yz_margin=L)
+    for s in (g, o):
+        s.set_fields(F)
+        s.set_particles(xi, u, w, ids)
+    g.step(1)
+    o.step(1)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+    n0 = g.info()["np"]
+    for _ in range(4):
+        g.step(1)
+        o.step(1)
+        assert g.info()["np"] == o.info()["np"]
+    assert g.info()["np"] < n0  # fast particles reached the layers and were absorbed
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+    with pytest.raises(pic.PicError):  # a particle may not start inside a layer
+        g.set_particles(np.array([[5.0], [L - 0.5], [14.0]]), np.zeros((3, 1)), np.array([1e-3]))
+
+
+def test_pml_window_run_and_checkpoint(tmp_path):
+    cfg = dict(_window_cfg(), pml=6)  # the laser's wings reach into the layers
+    g, o = make_gpu(cfg), make_oracle(cfg)
+    compare_particles(g.particles(), o.particles(), 1e-15)
+    compare_fields(g, o, 1e-12)
+    g.step(10)
+    o.step(10)
+    path = str(tmp_path / "pml.ckpt")
+    pic.pic_save(g.h, path)
+    g.step(30)
+    o.step(30)
+    ig, io = g.info(), o.info()
+    assert ig["shifts"] == io["shifts"] == 40 and ig["np"] == io["np"]
+    _compare_diags(_diags(g, cfg["nx"]), _diags(o, cfg["nx"]), 1e-6)
+    compare_particles(g.particles(), o.particles(), 1e-6)
+    b = make_gpu(cfg)  # resume from the checkpoint: the layers' memory comes back too
+    pic.pic_load(b.h, path)
+    b.step(30)
+    compare_particles(g.particles(), b.particles(), 1e-12)
+    compare_fields(g, b, 1e-12)
+    g32 = make_gpu(cfg, precision="fp32")
+    g32.step(40)
+    d32, d64 = _diags(g32, cfg["nx"]), _diags(g, cfg["nx"])
+    assert np.linalg.norm(d32["lineout"] - d64["lineout"]) <= 0.01 * np.linalg.norm(d64["lineout"])
+    assert abs(d32["energy"] / d64["energy"] - 1) <= 0.01
+
+
+def test_pml_batched_equals_single_fp32():
+    cfg = dict(_window_cfg(), pml=6)
+    single = make_gpu(cfg, precision="fp32")
+    member = make_gpu(cfg, precision="fp32")
+    b = pic.pic_batch_create([member.h])
+    try:
+        pic.pic_batch_step(b, 15)
+        single.step(15)
+        assert member.info()["np"] == single.info()["np"]
+        e_b = pic.pic_batch_diag(b, 0, pic.PIC_DIAG_FIELD_ENERGY)[0]
+        assert abs(e_b / single.diag("field_energy")[0] - 1) < 1e-4
+    finally:
+        pic.pic_batch_destroy(b)
