@@ -3,6 +3,7 @@
 // kernels of one step on the handle's stream, keeps the moving-window
 // accumulator in FP64 on the host and checks the device error word.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only; ranges cost nothing unless a tool is attached
 
 #include <algorithm>
 #include <cmath>
@@ -91,14 +92,20 @@ cudaEvent_t take_event(pic_t* h) {
   return e;
 }
 
+// Per-group event timing (when enabled) and an NVTX range named for the group,
+// so that profilers can select one part of the step.
 struct GroupTimer {
   pic_t* h;
   int group;
   cudaEvent_t a = nullptr;
   GroupTimer(pic_t* hh, int g) : h(hh), group(g) {
+    static const char* const names[4] = {"pic:gather_push_deposit", "pic:field_update", "pic:window_inject_bin",
+                                         "pic:other"};
+    nvtxRangePushA(names[g]);
     if (h->profiling && (a = take_event(h))) cudaEventRecord(a, h->stream);
   }
   ~GroupTimer() {
+    nvtxRangePop();
     if (!a) return;
     cudaEvent_t b = take_event(h);
     if (!b) {

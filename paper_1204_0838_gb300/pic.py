@@ -370,8 +370,9 @@ class Sim:
 
     def __init__(self, nx, ny, nz, dx, dy, dz, lambda0, x0=0.0, periodic_x=True,
                  precision="fp64", seed=12040838, dt=0.0, window=None, track_ids=False,
-                 max_particles=0, use_torch=True, solver="perfect", pml=0):
-        self._mem = TorchMemory() if use_torch else None
+                 max_particles=0, use_torch=True, solver="perfect", pml=0, memory=None):
+        # memory: an object with a pic_alloc `struct` (default: TorchMemory)
+        self._mem = memory if memory is not None else (TorchMemory() if use_torch else None)
         g = pic_grid(nx, ny, nz, dx, dy, dz, lambda0, x0,
                      PIC_FP64 if precision == "fp64" else PIC_FP32,
                      PIC_BC_PERIODIC if periodic_x else PIC_BC_OPEN,

@@ -463,3 +463,47 @@ def test_pml_batched_equals_single_fp32():
         assert abs(e_b / single.diag("field_energy")[0] - 1) < 1e-4
     finally:
         pic.pic_batch_destroy(b)
+
+
+# ---------------------------------------------------------------------------
+# failure injection on the host: device allocations that fail part-way
+# ---------------------------------------------------------------------------
+class _FailingMemory(pic.TorchMemory):
+    """pic_alloc hooks that grant `budget` allocations and then refuse."""
+
+    def __init__(self, budget):
+        super().__init__()
+        self.budget = budget
+
+    def _alloc(self, nbytes, ctx):
+        if self.budget <= 0:
+            return None
+        self.budget -= 1
+        return super()._alloc(nbytes, ctx)
+
+
+def test_allocation_failure_is_reported_and_leaves_the_device_usable():
+    codes = []
+    for budget in range(0, 24):
+        mem = _FailingMemory(budget)
+        g = None
+        try:
+            g = pic.Sim(32, 28, 28, LAM / 8, LAM / 4, LAM / 4, LAM, periodic_x=False, memory=mem, pml=6,
+                        window=(1.0, 0.0))
+            g.add_species([-1.0, 1.0], [0.01, 0.01], 2, loading="lattice")
+            g.add_laser(2.0, 2e-6, 4e-15, LAM, 0.0, 2e-14)
+            g.step(3)
+            g.diag("field_energy")
+            codes.append(0)
+        except pic.PicError as e:
+            codes.append(e.code)
+        finally:
+            if g is not None:
+                g.close()
+        assert not mem._live  # everything the handle got was given back
+    assert set(codes) <= {0, -3} and -3 in codes and codes[-1] == 0, codes
+    g, o = _pair((32, 8, 8), True)  # the device is unharmed
+    _set_random(g, o, (32, 8, 8), 2000, seed=30, periodic=True)
+    g.step(1)
+    o.step(1)
+    compare_fields(g, o, 1e-10)
