@@ -34,6 +34,11 @@ UNIT = "particle-steps/s"
 # weights 138, gather 882, Boris 54, position 17, deposit 522 (FMA = 2 flop).
 FLOP_PER_PARTICLE = 1613
 BYTES_PER_PARTICLE = {"fp64": 112, "fp32": 60}  # SoA record read once, written once
+# DRAM bytes (read + write) per particle of k_push_tiled, from one ncu capture
+# of the current kernel on a plasma-filled 256x128x128 window with the
+# full-size tile shapes (profiles/k_push_tiled_small_fp64_fp32.md); traffic
+# per launch scales with the particles processed.
+NCU_TRAFFIC_PER_PARTICLE = {"fp64": 1315.573248e6 / 8224822, "fp32": 689.543168e6 / 8224822}
 
 
 def _args():
@@ -47,7 +52,8 @@ def _args():
     ap.add_argument("--start-step", type=int, default=-1)
     ap.add_argument("--crop", default="", help="nx,ny,nz (profiling small cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true", help="keep the default 8x8x8 tiles")
+    ap.add_argument("--no-autotune", action="store_true", help="no tile search (default or --tile tiles)")
+    ap.add_argument("--tile", default="", help="tx,ty,tz: fixed tile shape (implies --no-autotune)")
     return ap.parse_args()
 
 
@@ -240,8 +246,13 @@ def run_ours(args):
                 window=cfg["window"])
     g.add_species(cfg["prof_x"], cfg["prof_n"], cfg["ppc"], loading=cfg["loading"])
     g.add_laser(cfg["a0"], cfg["waist"], cfg["fwhm"], cfg["lambda0"], cfg["x_focus"], cfg["t_peak"])
-    tile = (8, 8, 8)
-    if not args.no_autotune:
+    if args.tile:
+        tile = tuple(int(v) for v in args.tile.split(","))
+        pic.pic_set_tiles(g.h, *tile)
+    elif args.no_autotune:
+        env = os.environ.get("PIC_TILE")
+        tile = tuple(int(v) for v in env.split(",")) if env else (8, 8, 8)
+    else:
         cache = os.environ.get("PIC_AUTOTUNE_CACHE", "/tmp/pic_autotune_%d.json" % os.getpid())
         tile, _ = pic.pic_autotune(g.h, 1, cache)
     for _ in range(args.warmup):
@@ -298,7 +309,10 @@ def run_ours(args):
     peak = _fp_peak_tflops(precision, peaks.get("sm_max_mhz", 2070.0))
     roofline = {"kernel": "k_push_tiled (gather + Boris + Esirkepov deposit)",
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": None,
+                "frac": achieved / peak if peak else None,
+                "traffic": NCU_TRAFFIC_PER_PARTICLE[precision] * per_launch_pushes,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per particle "
+                                  "(plasma-filled 256x128x128 capture) x particles per launch",
                 "peak_source": "derived: 152 SMs x %s FMA lanes x 2 flop x %.0f MHz max clock" % (
                     "128 FP32" if precision == "fp32" else "2 FP64", peaks.get("sm_max_mhz", 2070.0)),
                 "hbm_achieved_gbs": BYTES_PER_PARTICLE[precision] * per_launch_pushes / avg_s / 1e9
@@ -404,7 +418,8 @@ def run_batch(args):
             "particles": int(sum(g.info()["np"] for g in sims)),
             "roofline": {"kernel": "k_push_tiled (FP32), one host-driven step per member",
                          "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "frac": achieved / peak if peak else None,
+                         "traffic": None,  # no capture of these member shapes (1-2 ppc, other cells)
                          "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x max clock"},
             "clocks": clk,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8,
