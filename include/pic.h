@@ -90,7 +90,8 @@ typedef struct pic_alloc {
 } pic_alloc;
 
 typedef struct pic_grid {
-  int nx, ny, nz;       /* cells of the window along x, y, z                   */
+  int nx, ny, nz;       /* cells of the window along x, y, z: nx >= 16,
+                           ny, nz >= 4, nx, ny <= 65535, nx ny nz < 2^31      */
   double dx, dy, dz;    /* metres; dx <= dy and dx <= dz (Sec. 2 constraint)   */
   double lambda0;       /* metres; reference wavelength: omega0 and n_c        */
   double x0;            /* metres; lab-frame x of node 0 at t = 0              */

@@ -63,6 +63,9 @@ void dfree(pic_t* h, void* p) {
     cudaFree(p);
 }
 
+// k_e_update: one thread per cell, blocks of 256 along z, block (., j, i).
+dim3 e_update_grid(const pic_t* h) { return dim3((h->nz + 255) / 256, h->ny, h->nx); }
+
 int grid_for(long long n, int per_block = 256, int cap = 152 * 32) {
   long long b = (n + per_block - 1) / per_block;
   if (b < 1) b = 1;
@@ -490,8 +493,8 @@ int field_first_half(pic_t* h) {
   }
   GroupTimer tm(h, G_FIELD);
   counted(h, G_FIELD);
-  k_e_update<T><<<grid_for(h->ncell), 256, 0, h->stream>>>(geom<T>(h), fields<T>(h), curl_view<T>(h),
-                                                           field_coef<T>(h), pml_view<T>(h));
+  k_e_update<T><<<e_update_grid(h), 256, 0, h->stream>>>(geom<T>(h), fields<T>(h), curl_view<T>(h),
+                                                         field_coef<T>(h), pml_view<T>(h));
   CK(h, cudaGetLastError());
   return PIC_OK;
 }
@@ -799,6 +802,7 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
   if (!g || !out) return PIC_ERR_ARG;
   *out = nullptr;
   if (g->nx < 16 || g->ny < 4 || g->nz < 4) return PIC_ERR_ARG;
+  if (g->nx > 65535 || g->ny > 65535) return PIC_ERR_ARG;  // launch grid extents of the field kernels
   if ((long long)g->nx * g->ny * g->nz > 0x7fffffffLL) return PIC_ERR_ARG;
   if (!(g->dx > 0 && g->dy > 0 && g->dz > 0 && g->lambda0 > 0)) return PIC_ERR_ARG;
   if (g->dx > g->dy || g->dx > g->dz) return PIC_ERR_ARG;  // Sec. 2: dx <= dy, dz
@@ -1780,7 +1784,7 @@ int enqueue_step_dyn(pic_t* h, cudaStream_t s, int cur, long long* kernels) {
   k_push_tiled<T><<<tl.n, 256, tiled_smem_bytes<T>(tl), s>>>(g, tl, f, parts<T>(h, cur), h->tstart[cur],
                                                             (int)h->capacity, h->keys, h->tcnt, hq, (T)h->q, 0,
                                                             x_lo(h), x_hi(h), h->d_pushed, h->d_ctrl + 2);
-  k_e_update<T><<<grid_for(n), 256, 0, s>>>(g, f, curl_view<T>(h), fc, pml_view<T>(h));
+  k_e_update<T><<<e_update_grid(h), 256, 0, s>>>(g, f, curl_view<T>(h), fc, pml_view<T>(h));
   launch_curl<T>(h, g, 1, 0, h->nx, s);
   k_window_commit<<<1, 32, 0, s>>>(h->d_dyn);
   k_zero_front_slab<T><<<grid_for((long long)NCOMP * h->ny * h->nz), 256, 0, s>>>(gs, f, pml_view<T>(h));

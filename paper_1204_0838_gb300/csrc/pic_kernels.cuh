@@ -125,18 +125,18 @@ __device__ __forceinline__ T bhalf(const T* __restrict__ B, const T* __restrict_
   return B[id] - hdt * C[id];
 }
 
+// Launch: grid (ceil(nz / blockDim.x), ny, nx), one thread per cell; k from
+// the thread, j and the window-relative slab i from the block (no division).
 template <typename T>
 __global__ void __launch_bounds__(256) k_e_update(Geom<T> g, Fields<T> f, Fields<T> cc, FieldCoef<T> fc, Pml<T> pm) {
   if (!dyn_prologue(g)) return;
   const int nyz = g.nyz;
-  const long long ncell = (long long)g.nx * nyz;
   const T *Bx = f.c[BX], *By = f.c[BY], *Bz = f.c[BZ];
   const T *Cx = cc.c[0], *Cy = cc.c[1], *Cz = cc.c[2];
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q / nyz);
-    const int r = (int)(q - (long long)i * nyz);
-    const int j = r / g.nz, k = r - j * g.nz;
+  {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+    if (k >= g.nz) return;
+    const int r = j * g.nz + k;
     const int s = slab_of(g, i), sm = slab_of(g, i - 1);
     const size_t id = (size_t)s * nyz + r;
     const T bx = Bx[id] - fc.hdt * Cx[id];
@@ -226,13 +226,35 @@ __global__ void __launch_bounds__(256) k_curl_tiled(Geom<T> g, Smooth<T> S, Fiel
       if (j < 0 || j >= g.ny || k < 0 || k >= g.nz) s = -1;
       j = min(max(j, 0), g.ny - 1);
       k = min(max(k, 0), g.nz - 1);
-    } else {
-      j = wrapi(j, g.ny);  // blocks may exceed small ny, nz
-      k = wrapi(k, g.nz);
+    } else {  // periodic; a block may exceed a small ny or nz more than once
+      j = j < 0 ? j + g.ny : (j >= g.ny ? j - g.ny : j);
+      k = k < 0 ? k + g.nz : (k >= g.nz ? k - g.nz : k);
+      if ((unsigned)j >= (unsigned)g.ny) j = wrapi(j, g.ny);
+      if ((unsigned)k >= (unsigned)g.nz) k = wrapi(k, g.nz);
     }
     const size_t gi = (size_t)(s < 0 ? 0 : s) * g.nyz + (size_t)j * g.nz + k;
 #pragma unroll
     for (int c = 0; c < 3; ++c) sE[c * CE_N + q] = s < 0 ? T(0) : f.c[EX + c][gi];
+  }
+  // Read what the output step needs from global memory (C, and B in mode 1)
+  // now, so that these loads overlap the shared-memory smoothing below.
+  // blockDim.x is 256: each thread owns kPer cells of the block.
+  constexpr int kPer = CB_X * CB_Y * CB_Z / 256;
+  static_assert(CB_X * CB_Y * CB_Z % 256 == 0, "whole cells per thread");
+  T pb[kPer][3], pc[kPer][3];
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int q = tid + 256 * t;
+    const int lz = q % CB_Z, r = q / CB_Z;
+    const int ly = r % CB_Y, lx = r / CB_Y;
+    const int i = bx + lx, j = by + ly, k = bz + lz;
+    const bool in = i < i0 + ni && j < g.ny && k < g.nz;
+    const size_t id = in ? (size_t)slab_of(g, i) * g.nyz + (size_t)j * g.nz + k : 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      pc[t][c] = in && mode == 1 ? cc.c[c][id] : T(0);
+      pb[t][c] = in && mode == 1 ? f.c[BX + c][id] : T(0);
+    }
   }
   __syncthreads();
 
@@ -280,8 +302,9 @@ __global__ void __launch_bounds__(256) k_curl_tiled(Geom<T> g, Smooth<T> S, Fiel
   }
   __syncthreads();
 
-  const int cells = CB_X * CB_Y * CB_Z;
-  for (int q = tid; q < cells; q += blockDim.x) {
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int q = tid + 256 * t;
     const int lz = q % CB_Z, r = q / CB_Z;
     const int ly = r % CB_Y, lx = r / CB_Y;
     const int i = bx + lx, j = by + ly, k = bz + lz;
@@ -329,9 +352,9 @@ __global__ void __launch_bounds__(256) k_curl_tiled(Geom<T> g, Smooth<T> S, Fiel
     const T cx = dyEz - dzEy, cy = dzEx - dxEz, cz = dxEy - dyEx;
     const size_t id = (size_t)slab * g.nyz + (size_t)j * g.nz + k;
     if (mode == 1) {
-      f.c[BX][id] = (f.c[BX][id] - fc.hdt * cc.c[0][id]) - fc.hdt * cx;
-      f.c[BY][id] = (f.c[BY][id] - fc.hdt * cc.c[1][id]) - fc.hdt * cy;
-      f.c[BZ][id] = (f.c[BZ][id] - fc.hdt * cc.c[2][id]) - fc.hdt * cz;
+      f.c[BX][id] = (pb[t][0] - fc.hdt * pc[t][0]) - fc.hdt * cx;
+      f.c[BY][id] = (pb[t][1] - fc.hdt * pc[t][1]) - fc.hdt * cy;
+      f.c[BZ][id] = (pb[t][2] - fc.hdt * pc[t][2]) - fc.hdt * cz;
     }
     cc.c[0][id] = cx;
     cc.c[1][id] = cy;

@@ -369,6 +369,21 @@ __global__ void k_scatter(Parts<T> src, const int* __restrict__ keys, const int*
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int pi = base + threadIdx.x;
     const int key = pi < n ? keys[pi] : -2;
+    // read the record before reserving its slot, so that these loads overlap
+    // the reservation's atomic round trip instead of following it
+    int cell = 0;
+    T o[3] = {T(0), T(0), T(0)}, u[3] = {T(0), T(0), T(0)}, w = T(0);
+    uint32_t id = 0;
+    if (key >= 0) {
+      cell = src.cell[pi];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        o[d] = src.o[d][pi];
+        u[d] = src.u[d][pi];
+      }
+      w = src.w[pi];
+      if (src.id) id = src.id[pi];
+    }
     int off;
     const int rank = warp_count(fill, key, true, &off);
     if (key >= 0) {
@@ -377,14 +392,14 @@ __global__ void k_scatter(Parts<T> src, const int* __restrict__ keys, const int*
         atomicOr(err, 2);
         continue;
       }
-      dst.cell[slot] = src.cell[pi];
+      dst.cell[slot] = cell;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        dst.o[d][slot] = src.o[d][pi];
-        dst.u[d][slot] = src.u[d][pi];
+        dst.o[d][slot] = o[d];
+        dst.u[d][slot] = u[d];
       }
-      dst.w[slot] = src.w[pi];
-      if (dst.id) dst.id[slot] = src.id[pi];
+      dst.w[slot] = w;
+      if (dst.id) dst.id[slot] = id;
     }
   }
 }
