@@ -63,8 +63,13 @@ void dfree(pic_t* h, void* p) {
     cudaFree(p);
 }
 
-// k_e_update: one thread per cell, blocks of 256 along z, block (., j, i).
-dim3 e_update_grid(const pic_t* h) { return dim3((h->nz + 255) / 256, h->ny, h->nx); }
+// k_e_update: one thread per cell, blocks of up to 256 threads along z (a
+// multiple of 32 covering nz when it is shorter), block (., j, i).
+int e_update_block(const pic_t* h) { return std::min(256, (h->nz + 31) / 32 * 32); }
+dim3 e_update_grid(const pic_t* h) {
+  const int b = e_update_block(h);
+  return dim3((h->nz + b - 1) / b, h->ny, h->nx);
+}
 
 int grid_for(long long n, int per_block = 256, int cap = 152 * 32) {
   long long b = (n + per_block - 1) / per_block;
@@ -493,7 +498,7 @@ int field_first_half(pic_t* h) {
   }
   GroupTimer tm(h, G_FIELD);
   counted(h, G_FIELD);
-  k_e_update<T><<<e_update_grid(h), 256, 0, h->stream>>>(geom<T>(h), fields<T>(h), curl_view<T>(h),
+  k_e_update<T><<<e_update_grid(h), e_update_block(h), 0, h->stream>>>(geom<T>(h), fields<T>(h), curl_view<T>(h),
                                                          field_coef<T>(h), pml_view<T>(h));
   CK(h, cudaGetLastError());
   return PIC_OK;
@@ -1784,7 +1789,7 @@ int enqueue_step_dyn(pic_t* h, cudaStream_t s, int cur, long long* kernels) {
   k_push_tiled<T><<<tl.n, 256, tiled_smem_bytes<T>(tl), s>>>(g, tl, f, parts<T>(h, cur), h->tstart[cur],
                                                             (int)h->capacity, h->keys, h->tcnt, hq, (T)h->q, 0,
                                                             x_lo(h), x_hi(h), h->d_pushed, h->d_ctrl + 2);
-  k_e_update<T><<<e_update_grid(h), 256, 0, s>>>(g, f, curl_view<T>(h), fc, pml_view<T>(h));
+  k_e_update<T><<<e_update_grid(h), e_update_block(h), 0, s>>>(g, f, curl_view<T>(h), fc, pml_view<T>(h));
   launch_curl<T>(h, g, 1, 0, h->nx, s);
   k_window_commit<<<1, 32, 0, s>>>(h->d_dyn);
   k_zero_front_slab<T><<<grid_for((long long)NCOMP * h->ny * h->nz), 256, 0, s>>>(gs, f, pml_view<T>(h));
