@@ -50,7 +50,9 @@ extern "C" {
 #define PIC_ERR_OOM -3      /* device allocation failed                          */
 #define PIC_ERR_CAPACITY -4 /* particle capacity exceeded (injection/loading)    */
 #define PIC_ERR_TIMEOUT -5  /* a bounded device-side wait gave up                */
-#define PIC_ERR_NUMERIC -6  /* a diagnostic found NaN or Inf                     */
+#define PIC_ERR_NUMERIC -6  /* a diagnostic found NaN or Inf, or a step met a
+                               particle with a non-finite momentum (reported
+                               once; that particle was absorbed)              */
 #define PIC_ERR_STATE -7    /* call not valid in the handle's current state      */
 
 /* ---- enumerations ---- */

@@ -673,6 +673,13 @@ int check_device_error(pic_t* h) {
     return fail(h, PIC_ERR_CAPACITY, "particle capacity exceeded during loading/injection");
   }
   if (ctrl[2] & 6) return fail(h, PIC_ERR_STATE, "tile bookkeeping error in the particle binning");
+  if (ctrl[2] & 8) {
+    // reported once: the offending particles were absorbed
+    const int zero = 0;
+    CK(h, cudaMemcpyAsync(h->d_ctrl + 2, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return fail(h, PIC_ERR_NUMERIC, "non-finite particle momentum: the particle was absorbed");
+  }
   return PIC_OK;
 }
 

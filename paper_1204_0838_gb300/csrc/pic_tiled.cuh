@@ -183,7 +183,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom
       u[0] = um[0] + (py * sv[2] - pz * sv[1]) + h * E[0];
       u[1] = um[1] + (pz * sv[0] - px * sv[2]) + h * E[1];
       u[2] = um[2] + (px * sv[1] - py * sv[0]) + h * E[2];
-      const T ig = rsqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);  // 1 / gamma
+      T ig = rsqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);  // 1 / gamma
+      // a non-finite momentum (a blown-up state) is reported and the particle
+      // absorbed without moving or depositing, so that the fields stay finite
+      const bool bad = !(ig > T(0));
+      if (bad) {
+        atomicOr(err, 8);
+        ig = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) u[d] = T(0);
+      }
 
       // position update (cell + offset), |move| < 1 cell per axis
       T o1[3];
@@ -232,7 +241,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom
           DS[d][m] = a1 - a0;
         }
       }
-      const T qw = q * p.w[pi];
+      const T qw = bad ? T(0) : q * p.w[pi];
 #pragma unroll
       for (int comp = 0; comp < 3; ++comp) {
         // axis `comp` carries the running sum; (b, c) are the other two axes
@@ -292,6 +301,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom
       }
       // absorbing layers: a particle that leaves the y, z cells [L, n - L) is absorbed
       if (g.pml && (n1 < g.pml || n1 >= g.ny - g.pml || n2 < g.pml || n2 >= g.nz - g.pml)) key = -1;
+      if (bad) key = -1;
       keys[pi] = key;
       }
     }

@@ -272,6 +272,17 @@ def test_error_codes():
     with pytest.raises(pic.PicError) as e:
         g.set_particles(np.array([[0.5], [1.0], [1.0]]), np.zeros((3, 1)), np.ones(1))
     assert e.value.code == -1  # x cell 0 is outside the open-x allowed range
+    # a particle whose momentum overflows: reported once, absorbed, fields stay finite
+    g2 = pic.Sim(32, 8, 8, LAM / 8, LAM / 4, LAM / 2, LAM, periodic_x=False)
+    xi = np.array([[10.5, 12.5], [3.5, 3.5], [3.5, 3.5]])
+    u = np.array([[1e300, 0.1], [0.0, 0.0], [0.0, 0.0]])
+    g2.set_particles(xi, u, np.array([1e-3, 1e-3]))
+    with pytest.raises(pic.PicError) as e:
+        g2.step(1)
+    assert e.value.code == -6
+    assert g2.info()["np"] == 1
+    g2.step(1)
+    assert np.isfinite(g2.fields()).all()
 
 
 def test_autotune_restores_state_and_keeps_results(tmp_path):
