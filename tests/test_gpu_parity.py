@@ -518,3 +518,45 @@ def test_allocation_failure_is_reported_and_leaves_the_device_usable():
     g.step(1)
     o.step(1)
     compare_fields(g, o, 1e-10)
+
+
+# ---------------------------------------------------------------------------
+# further edge cases: an explicit dt below c dt = dx, other loadings, a window
+# slower than c (fractional shifts with the perfect-dispersion solver)
+# ---------------------------------------------------------------------------
+def test_explicit_smaller_dt_parity():
+    shape = (32, 12, 10)
+    dt = 0.6 * (LAM / 8) / C0
+    g = pic.Sim(*shape, LAM / 8, LAM / 3, LAM / 2, LAM, periodic_x=False, track_ids=True, dt=dt)
+    o = O.Sim(*shape, LAM / 8, LAM / 3, LAM / 2, LAM, periodic_x=False, dt=dt)
+    assert abs(g.info()["dt"] / g.info()["dx"] - 0.6) < 1e-12
+    _set_random(g, o, shape, 8000, seed=41, periodic=False)
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+
+
+@pytest.mark.parametrize("ppc,loading", [(4, "lattice"), (8, "lattice"), (3, "random")])
+def test_loading_parity_other_ppc(ppc, loading):
+    cfg = dict(W.config("c0"), ppc=ppc, loading=loading)
+    cfg["nx"], cfg["ny"], cfg["nz"] = 40, 12, 12
+    g, o = make_gpu(cfg, laser=False), make_oracle(cfg, laser=False)
+    assert g.info()["np"] == o.info()["np"] > 0
+    compare_particles(g.particles(), o.particles(), 1e-15)
+    g.step(2)
+    o.step(2)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+
+
+def test_window_slower_than_c_fractional_shifts():
+    cfg = dict(_window_cfg(), window=(0.9, 0.0))
+    g, o = make_gpu(cfg), make_oracle(cfg)
+    g.step(30)
+    o.step(30)
+    ig, io = g.info(), o.info()
+    assert ig["shifts"] == io["shifts"] and 26 <= ig["shifts"] <= 27  # 30 steps x 0.9 cell
+    assert ig["np"] == io["np"]
+    _compare_diags(_diags(g, cfg["nx"]), _diags(o, cfg["nx"]), 1e-6)
