@@ -5,6 +5,10 @@
   longitudinal field is negative.  Reading used here: on the on-axis Ex
   lineout, the contiguous run of cells with Ex < 0 that contains the most
   negative Ex (the peak accelerating field at the rear of the first bucket).
+- bubble_scalings: the blowout-regime estimates of Sec. 1 (energy gain at
+  dephasing, Eq. (Ed); dephasing length, Eq. (Ld); critical power for
+  relativistic self-focusing; accelerating-phase length, Eq. (Rb)) from the
+  plasma density, the laser wavelength and the laser power.
 - initial_cells: particle ids (PIC_FLAG_TRACK_IDS) encode the lab cell and
   slot a particle was loaded in (id = ((L * ny + j) * nz + k) * ppc + slot);
   decoding them gives the initial positions to cell resolution, i.e. the
@@ -49,3 +53,21 @@ def initial_positions(ids, ppc, grid):
     y = (j + 0.5 - 0.5 * grid["ny"]) * grid["dy"]
     z = (k + 0.5 - 0.5 * grid["nz"]) * grid["dz"]
     return x_in, np.hypot(y, z)
+
+
+def bubble_scalings(n0_per_cm3, lambda0_m, power_W):
+    """Sec. 1 estimates for a laser of power P and wavelength lambda0 in a
+    plasma of density n0, with gamma_g = omega0 / omega_pe = sqrt(n_c / n0):
+    E_d ~ 2.7 gamma_g^(4/3) P_TW^(1/3) MeV, L_d ~ 0.6 lambda0 gamma_g^(8/3)
+    P_TW^(1/6), P_cr = 16.2 gamma_g^2 GW, L_acc ~ 0.9 lambda0 gamma_g^(2/3)
+    P_TW^(1/6).  Returns SI values (m, W) and MeV."""
+    c, qe, me, eps0 = 299792458.0, 1.602176634e-19, 9.1093837015e-31, 8.8541878128e-12
+    omega0 = 2.0 * np.pi * c / lambda0_m
+    n_c = eps0 * me * omega0 ** 2 / qe ** 2  # 1/m^3
+    gamma_g = float(np.sqrt(n_c / (n0_per_cm3 * 1e6)))
+    p_tw = power_W / 1e12
+    return {"gamma_g": gamma_g, "n0_over_nc": n0_per_cm3 * 1e6 / n_c,
+            "P_cr_W": 16.2e9 * gamma_g ** 2,
+            "E_d_MeV": 2.7 * gamma_g ** (4.0 / 3.0) * p_tw ** (1.0 / 3.0),
+            "L_d_m": 0.6 * lambda0_m * gamma_g ** (8.0 / 3.0) * p_tw ** (1.0 / 6.0),
+            "L_acc_m": 0.9 * lambda0_m * gamma_g ** (2.0 / 3.0) * p_tw ** (1.0 / 6.0)}

@@ -822,3 +822,24 @@ def test_pml_loading_fills_only_the_interior():
         O.Sim(6, 14, 24, LAM / 8, LAM / 4, LAM / 4, LAM, periodic_x=True, pml=6)
     with pytest.raises(ValueError):
         O.Sim(6, 24, 24, LAM / 8, LAM / 4, LAM / 4, LAM, periodic_x=True, pml=2)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 1 blowout-regime estimates (host analysis helper) against the values the
+# paper prints for its own parameters (tests/golden/paper_sec1_scalings.txt)
+# ---------------------------------------------------------------------------
+def test_bubble_scalings_match_the_printed_values(golden_dir):
+    from paper_1204_0838_gb300 import analysis as A
+    rows = [l.split() for l in open(os.path.join(golden_dir, "paper_sec1_scalings.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 6
+    for case, n0, lam, pw, q, val, tol in rows:
+        r = A.bubble_scalings(float(n0), float(lam), float(pw))
+        got = float(pw) / r["P_cr_W"] if q == "P_over_Pcr" else r[q]
+        assert abs(got / float(val) - 1) <= float(tol), (case, q, got, val)
+    # doubling the energy at fixed power: density / 2^1.5, length x 4, bubble x 2^0.5^(2/3)
+    a = A.bubble_scalings(3.5e18, 0.8e-6, 200e12)
+    b = A.bubble_scalings(3.5e18 / 2 ** 1.5, 0.8e-6, 200e12)
+    assert abs(b["E_d_MeV"] / a["E_d_MeV"] - 2) < 1e-12
+    assert abs(b["L_d_m"] / a["L_d_m"] - 4) < 1e-12
+    assert abs(b["L_acc_m"] / a["L_acc_m"] - 1.41) < 0.01
