@@ -560,3 +560,25 @@ def test_window_slower_than_c_fractional_shifts():
     assert ig["shifts"] == io["shifts"] and 26 <= ig["shifts"] <= 27  # 30 steps x 0.9 cell
     assert ig["np"] == io["np"]
     _compare_diags(_diags(g, cfg["nx"]), _diags(o, cfg["nx"]), 1e-6)
+
+
+def test_window_with_laser_and_no_plasma():
+    cfg = _window_cfg()
+    g, o = make_gpu(cfg, species=False), make_oracle(cfg, species=False)
+    g.step(25)
+    o.step(25)
+    assert g.info()["np"] == 0 and g.info()["shifts"] == o.info()["shifts"] == 25
+    compare_fields(g, o, 1e-10)
+
+
+def test_largest_grid_extent_along_x():
+    # nx at the C-ABI's limit (65535 slabs: the x extent of the field kernels' launch grids)
+    shape = (65535, 4, 4)
+    g, o = _pair(shape, True, dy=LAM / 2, dz=LAM / 2)
+    _set_random(g, o, shape, 20000, seed=51, periodic=True)
+    g.step(2)
+    o.step(2)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+    with pytest.raises(pic.PicError):
+        pic.Sim(65536, 4, 4, LAM / 8, LAM / 2, LAM / 2, LAM)
