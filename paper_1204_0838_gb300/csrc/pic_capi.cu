@@ -1671,8 +1671,8 @@ int autotune_impl(pic_t* h, int steps, const char* cache_path, int out3[3], doub
     *best_ms = -1.0;
     return PIC_OK;
   }
-  static const int cand[][3] = {{8, 8, 8}, {16, 8, 8}, {8, 4, 4}, {16, 4, 4}, {32, 4, 4},
-                                {4, 8, 8}, {8, 8, 4}, {16, 8, 4}, {4, 4, 4}, {12, 6, 6}};
+  static const int cand[][3] = {{8, 8, 8}, {16, 8, 8}, {8, 8, 16}, {4, 8, 16}, {8, 4, 4}, {16, 4, 4},
+                                {32, 4, 4}, {4, 8, 8}, {8, 8, 4}, {16, 8, 4}, {4, 4, 4}, {12, 6, 6}};
   const Tiles orig = h->tiles;
   double best = 1e300;
   int bi = -1;
