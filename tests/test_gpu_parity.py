@@ -582,3 +582,22 @@ def test_largest_grid_extent_along_x():
     compare_fields(g, o, 1e-10)
     with pytest.raises(pic.PicError):
         pic.Sim(65536, 4, 4, LAM / 8, LAM / 2, LAM / 2, LAM)
+
+
+def test_particle_capacity_grows_between_calls():
+    # set_particles sizes the buffers to the particles given; the next call
+    # finds them more than 80 % full and grows them by half (state kept)
+    shape = (32, 16, 16)
+    g, o = _pair(shape, True)
+    _set_random(g, o, shape, 20000, seed=61, periodic=True)
+    cap0 = g.info()["capacity"]
+    assert cap0 == 20000
+    g.step(1)
+    o.step(1)
+    assert g.info()["capacity"] > cap0
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+    g.step(2)
+    o.step(2)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
