@@ -107,13 +107,15 @@ struct Parts {
 // Cubic B-spline weights of the four nodes c-1, c, c+1, c+2 for a particle
 // at offset t in [0,1) of cell c (the uniform cubic B-spline evaluated at the
 // node distances 1+t, t, 1-t, 2-t).
+// With s = 1 - t: w0 = s^3/6, w1 = 2/3 - t^2 + t^3/2, w2 = 2/3 - s^2 + s^3/2,
+// w3 = t^3/6 (the kernel's two polynomial pieces at those distances).
 template <typename T>
 __device__ __forceinline__ void bspline3(T t, T w[4]) {
-  const T s = T(1) - t, t2 = t * t, t3 = t2 * t;
-  const T sixth = T(1) / T(6);
-  w[0] = s * s * s * sixth;
-  w[1] = (T(3) * t3 - T(6) * t2 + T(4)) * sixth;
-  w[2] = (T(3) * (t2 + t - t3) + T(1)) * sixth;
+  const T s = T(1) - t, t2 = t * t, s2 = s * s, t3 = t2 * t, s3 = s2 * s;
+  const T sixth = T(1) / T(6), two3 = T(2) / T(3);
+  w[0] = s3 * sixth;
+  w[1] = fma(t3, T(0.5), two3 - t2);
+  w[2] = fma(s3, T(0.5), two3 - s2);
   w[3] = t3 * sixth;
 }
 
