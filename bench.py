@@ -35,10 +35,11 @@ UNIT = "particle-steps/s"
 FLOP_PER_PARTICLE = 1613
 BYTES_PER_PARTICLE = {"fp64": 112, "fp32": 60}  # SoA record read once, written once
 # DRAM bytes (read + write) per particle of k_push_tiled, from one ncu capture
-# of the current kernel on a plasma-filled 256x128x128 window with the
-# full-size tile shapes (profiles/k_push_tiled_small_fp64_fp32.md); traffic
-# per launch scales with the particles processed.
-NCU_TRAFFIC_PER_PARTICLE = {"fp64": 1315.573248e6 / 8224822, "fp32": 689.543168e6 / 8224822}
+# of the current kernel on a plasma-filled 256x128x128 window with the tile
+# shapes the autotuner picks at full size (FP64 8x8x16, FP32 4x8x16;
+# profiles/k_push_tiled_small_fp64_fp32.md); traffic per launch scales with the
+# particles processed.
+NCU_TRAFFIC_PER_PARTICLE = {"fp64": 1310.100224e6 / 8224822, "fp32": 692.232960e6 / 8224822}
 
 
 def _args():
