@@ -70,6 +70,17 @@ __device__ __forceinline__ T gather_smem(const T* __restrict__ s, int SY, int SZ
   return ax;
 }
 
+// Comparisons of an offset against 0, 1/2 and 1.  In FP64 they are made on
+// the bit pattern with integer instructions, off the FP64 pipe that bounds
+// the push: for doubles of either sign the int64 view orders non-negative
+// values like the values and makes every negative value (and -0) negative.
+__device__ __forceinline__ bool lt_zero(double o) { return __double_as_longlong(o) < 0; }
+__device__ __forceinline__ bool ge_one(double o) { return __double_as_longlong(o) >= 0x3FF0000000000000LL; }
+__device__ __forceinline__ bool lt_half(double o) { return __double_as_longlong(o) < 0x3FE0000000000000LL; }
+__device__ __forceinline__ bool lt_zero(float o) { return o < 0.0f; }
+__device__ __forceinline__ bool ge_one(float o) { return o >= 1.0f; }
+__device__ __forceinline__ bool lt_half(float o) { return o < 0.5f; }
+
 // One CTA per tile.  keys[p] receives the particle's tile after the move (or
 // -1 when it leaves the open-x range once the window has moved to
 // origin_after); cnt_next[tile] counts the particles each tile will hold.
@@ -154,7 +165,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         bspline3(o0[d], wn[d]);
-        const bool lo = o0[d] < T(0.5);
+        const bool lo = lt_half(o0[d]);
         bspline3(lo ? o0[d] + T(0.5) : o0[d] - T(0.5), wh[d]);
         bn[d] = lc[d] - 1;
         bh[d] = lc[d] - (lo ? 2 : 1);
@@ -201,14 +212,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom
       for (int d = 0; d < 3; ++d) {
         T o = o0[d] + dtd[d] * u[d] * ig;
         int k = 0;
-        if (o < T(0)) {
+        if (lt_zero(o)) {
           o += T(1);
           k = -1;
-        } else if (o >= T(1)) {
+        } else if (ge_one(o)) {
           o -= T(1);
           k = 1;
         }
-        if (o >= T(1)) {
+        if (ge_one(o)) {
           o = T(0);
           k += 1;
         }
