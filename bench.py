@@ -39,7 +39,7 @@ BYTES_PER_PARTICLE = {"fp64": 112, "fp32": 60}  # SoA record read once, written 
 # shapes the autotuner picks at full size (FP64 8x8x16, FP32 4x8x16;
 # profiles/k_push_tiled_small_fp64_fp32.md); traffic per launch scales with the
 # particles processed.
-NCU_TRAFFIC_PER_PARTICLE = {"fp64": 1310.100224e6 / 8224822, "fp32": 692.232960e6 / 8224822}
+NCU_TRAFFIC_PER_PARTICLE = {"fp64": 1309.677824e6 / 8224822, "fp32": 691.607552e6 / 8224822}
 
 
 def _args():
