@@ -8,8 +8,8 @@
  * One step, all on one GPU in hand-written CUDA kernels:
  *   cubic-spline gather of E, B to each macroparticle (abstract and Sec. 3.1:
  *   third-order spline macroparticle shapes), relativistic Boris push,
- *   charge-conserving (Esirkepov) cubic current deposit (Sec. 2: "J is the
- *   electric current deposited from particle motion"), the perfect-dispersion
+ *   charge-conserving (Esirkepov) cubic current deposit (Sec. 2: the field
+ *   update takes its current from the particles' motion), the perfect-dispersion
  *   field update of Eq. (perfDispMaxwell) with the transversely smoothed curl
  *   of Sec. 2, and the moving window of Sec. 1.
  *

@@ -11,12 +11,12 @@
  * One step (stored E^n, B^n at integer time, u at half time, x at integer
  * time):
  *   1. gather E^n, B^n at x^n with the cubic spline shape (abstract, Sec. 3.1:
- *      "third-order splines");
+ *      third-order spline shapes for the macroparticles);
  *   2. relativistic Boris push u^{n-1/2} -> u^{n+1/2}, x^{n+1} = x^n + dt u/gamma
  *      (the PIC particle advance of Sec. 1);
  *   3. charge-conserving (Esirkepov) deposit of J^{n+1/2} from the motion
- *      x^n -> x^{n+1} ("J is the electric current deposited from particle
- *      motion", Sec. 2);
+ *      x^n -> x^{n+1} (Sec. 2: the field update takes its current from the
+ *      particles' motion);
  *   4. field update of Eq. (perfDispMaxwell), Sec. 2: B is advanced in two
  *      half steps with the smoothed curl of E, E in one step with the standard
  *      curl of B and the deposited J;
@@ -29,7 +29,7 @@
  *   - smoothing coefficients: the family in smoothing_coefficients() below,
  *     which has no dispersion along x for c dt = dx and is stable for every
  *     dx <= dy, dz (Sec. 2 constraint);
- *   - "third-order splines" = cubic B-spline, 4-node support;
+ *   - third-order spline shapes read as the cubic B-spline, 4-node support;
  *   - the same cubic weights at each field component's own staggered
  *     position for the gather;
  *   - Boris push and Esirkepov deposit (the paper names neither);

@@ -70,8 +70,9 @@ typedef struct {
 
 typedef struct or_sim or_sim;
 
-/* Set-up.  dt_si <= 0 selects c dt = dx (Sec. 2 with the abstract's
- * "proportionally larger time step").  Returns NULL on invalid arguments. */
+/* Set-up.  dt_si <= 0 selects c dt = dx (Sec. 2, with the abstract's time
+ * step enlarged in proportion to the coarse cell).  Returns NULL on invalid
+ * arguments. */
 or_sim* or_create(const or_grid* g, double dt_si, const or_window* w);
 void or_destroy(or_sim* s);
 int or_add_species(or_sim* s, const or_profile* prof, int ppc, double q, double m, int loading);

@@ -55,7 +55,7 @@ def test_splitmix64_published_outputs(golden_dir):
 
 
 # ---------------------------------------------------------------------------
-# P5: cubic spline (abstract / Sec. 3.1 "third-order splines")
+# P5: cubic spline (abstract / Sec. 3.1: third-order spline shapes)
 # ---------------------------------------------------------------------------
 def test_m4_matches_scipy_bspline_and_moments():
     rng = np.random.default_rng(1)
