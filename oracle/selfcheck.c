@@ -1,5 +1,5 @@
 /*
- * selfcheck.c -- a small driver that runs every path of the oracle once
+ * selfcheck.c -- a small program that runs every path of the oracle once
  * (periodic and open x, moving window, both laser modes, both solvers,
  * absorbing layers, every diagnostic, particle get/set), for a build with
  * the address and undefined-behaviour sanitizers.
