@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--instances", type=int, default=32, help="c3: batched instances")
     ap.add_argument("--start-step", type=int, default=-1)
     ap.add_argument("--crop", default="", help="nx,ny,nz (profiling small cases)")
+    ap.add_argument("--cold-start", action="store_true",
+                    help="load the plasma at rest at the start step instead of running up to it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="no tile search (default or --tile tiles)")
     ap.add_argument("--tile", default="", help="tx,ty,tz: fixed tile shape (implies --no-autotune)")
@@ -79,17 +81,37 @@ def reduce_over_ranks(ms, pushed, world_size):
     return float(t[0]), float(c[0])
 
 
+def _prerun_steps(start, nx, cold_start):
+    """Steps to run before the timed ones so that step `start` is reached in
+    the state of the real run.  Plasma enters at the front of a window moving
+    at c and leaves at the back nx steps later, so a state that has been
+    stepped for nx steps since any cold load is that of the run; a shorter run
+    (start < nx) is replayed from its empty box.  cold_start: load the plasma
+    that has entered by `start` at rest and step from there (quick profiling;
+    no wake yet, so faster than the real state)."""
+    return 0 if cold_start else min(start, nx)
+
+
 def _workload(args):
     from paper_1204_0838_gb300 import workloads as W
     start = args.start_step
     if start < 0:
         start = {"c0": 0, "c1": 900, "c2": 900, "c3": 450, "c4": 4500}[args.config]
     crop = tuple(int(v) for v in args.crop.split(",")) if args.crop else None
-    cfg = W.config(args.config, crop=crop, start_step=start)
-    return cfg, start
+    nx = W.config(args.config, crop=crop)["nx"]
+    pre = _prerun_steps(start, nx, args.cold_start)
+    cfg = W.config(args.config, crop=crop, start_step=start - pre)
+    return cfg, start, pre
 
 
-def _describe(cfg, start, precision):
+def _describe(cfg, start, precision, pre):
+    if pre == start:
+        state = "the run itself from its empty box (t = 0) to step %d, untimed" % start
+    elif pre > 0:
+        state = ("plasma loaded at rest at step %d, then %d untimed steps: every particle loaded at rest "
+                 "has left the window, so the state is the run's" % (start - pre, pre))
+    else:
+        state = "plasma that entered by step %d loaded at rest (cold start: no wake yet)" % start
     return {"workload": "%s: %dx%dx%d cells, dx=lambda0/%g, dy=dz=lambda0/%g, %d ppc %s, %s, "
             "a0=%g, %s, steps %d.. of the %d-step run" % (
                 cfg["name"], cfg["nx"], cfg["ny"], cfg["nz"], cfg["lambda0"] / cfg["dx"],
@@ -97,6 +119,7 @@ def _describe(cfg, start, precision):
                 "moving window at c" if cfg["window"] else "no window", cfg["a0"], precision,
                 start, cfg["steps"]),
             "grid": [cfg["nx"], cfg["ny"], cfg["nz"]], "ppc": cfg["ppc"], "start_step": start,
+            "state": state, "prerun_steps": pre,
             "precision": precision,
             "l2": "inputs larger than L2 (fields and particles are GBs), no flush"}
 
@@ -214,7 +237,7 @@ def run_reference(args):
         return
     from oracle import build as ob
     ob.build()
-    cfg, start = _workload(args)
+    cfg, start, pre = _workload(args)
     o, desc = _oracle_sample()
     _time_oracle(o, args.warmup)
     pushed, dt = _time_oracle(o, args.steps)
@@ -222,7 +245,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference", "config": _describe(cfg, start, "fp64"),
+            "data": "synthetic", "impl": "reference", "config": _describe(cfg, start, "fp64", pre),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": desc + "; each timed step is one step of this sample"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -240,13 +263,15 @@ def run_ours(args):
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     pb.build()
-    cfg, start = _workload(args)
+    cfg, start, pre = _workload(args)
     precision = cfg["precision"]
     g = pic.Sim(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"], cfg["lambda0"],
                 x0=cfg["x0"], periodic_x=cfg["periodic_x"], precision=precision, seed=cfg["seed"] + rank,
                 window=cfg["window"])
     g.add_species(cfg["prof_x"], cfg["prof_n"], cfg["ppc"], loading=cfg["loading"])
     g.add_laser(cfg["a0"], cfg["waist"], cfg["fwhm"], cfg["lambda0"], cfg["x_focus"], cfg["t_peak"])
+    for done in range(0, pre, 100):  # reach step `start` in the run's own state (untimed)
+        g.step(min(100, pre - done))
     if args.tile:
         tile = tuple(int(v) for v in args.tile.split(","))
         pic.pic_set_tiles(g.h, *tile)
@@ -323,7 +348,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32",
-            "data": "synthetic", "config": dict(_describe(cfg, start, precision), tile=list(tile)),
+            "data": "synthetic", "config": dict(_describe(cfg, start, precision, pre), tile=list(tile)),
             "particles": info["np"], "roofline": roofline, "clocks": clk,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32,
                     "note": "pic_step(1) + pic_diag(field energy) into a host buffer per step; "
@@ -362,12 +387,14 @@ def run_batch(args):
     cache = os.environ.get("PIC_AUTOTUNE_CACHE", "/tmp/pic_autotune_%d.json" % os.getpid())
     for c in cfgs:
         c = dict(c)
-        c["x0"] += start * c["dx"]
-        c["t_peak"] -= start * c["dx"] / W.C0
+        pre = _prerun_steps(start, c["nx"], args.cold_start)
+        c["x0"] += (start - pre) * c["dx"]
+        c["t_peak"] -= (start - pre) * c["dx"] / W.C0
         g = pic.Sim(c["nx"], c["ny"], c["nz"], c["dx"], c["dy"], c["dz"], c["lambda0"], x0=c["x0"],
                     periodic_x=False, precision="fp32", seed=c["seed"], window=c["window"])
         g.add_species(c["prof_x"], c["prof_n"], c["ppc"], loading=c["loading"])
         g.add_laser(c["a0"], c["waist"], c["fwhm"], c["lambda0"], c["x_focus"], c["t_peak"])
+        g.step(pre)  # every member reaches step `start` in its run's own state (untimed)
         tile, _ = pic.pic_autotune(g.h, 1, cache)
         tiles.append(tile)
         # one host-driven step per member with kernel timing: the roofline of the push kernel
@@ -414,6 +441,9 @@ def run_batch(args):
                                    "U[10,20] um, nx 256..768 x ny=nz 64..128, dx=lambda0/16, "
                                    "dy=dz=lambda0/3, 1-2 ppc, window at c, steps %d.. of 500; one "
                                    "CUDA graph launch per step; autotuned tiles" % (len(sims), start),
+                       "state": "each member loaded at rest at step %d - min(%d, nx) and run up to step %d "
+                                "(untimed): the run's own state" % (start, start, start) if not args.cold_start
+                       else "plasma loaded at rest at step %d (cold start)" % start,
                        "tiles": tiles, "cells": int(sum(c["nx"] * c["ny"] * c["nz"] for c in cfgs)),
                        "l2": "inputs larger than L2, no flush"},
             "particles": int(sum(g.info()["np"] for g in sims)),
