@@ -4,9 +4,12 @@ Default workload (c1): 1536x256x256 cells, dx = lambda0/24, dy = dz = lambda0/3,
 lambda0 = 0.8 um, 2 electrons per cell on a jittered lattice, n = 0.004 n_c
 behind a 50 um up-ramp, a0 = 4, 30 fs, 16 um waist, moving window at c, FP64.
 The timed steps are steps S..S+K of the 1000-step run, S = --start-step
-(default 900): the window and laser are placed where they are at step S with
-the plasma that has entered by then loaded cold, so every timed step pushes
-the particle count of the late run.  A step is the whole path: gather, Boris
+(default 900), taken in the run's own state: the run is replayed from its
+empty box up to S (S < nx), or run for nx steps from a load at rest at step
+S - nx, after which every particle loaded at rest has left the window.  Every
+timed step therefore pushes the particle count and the wake of the late run.
+--cold-start loads the plasma at rest at S instead (quick profiling; no wake
+yet, so it overstates the rate).  A step is the whole path: gather, Boris
 push, Esirkepov deposit, field update, window shift, absorption, injection.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]

@@ -45,3 +45,13 @@ def test_two_rank_reduction_matches_bench_contract():
 def test_single_rank_is_identity():
     import bench
     assert bench.reduce_over_ranks(5.0, 7, 1) == (5.0, 7.0)
+
+
+def test_bench_reaches_the_start_step_in_the_run_state():
+    import bench
+    # shorter than the window: the run is replayed from its empty box
+    assert bench._prerun_steps(900, 1536, False) == 900
+    # longer: nx steps after a load at rest flush every loaded particle out
+    assert bench._prerun_steps(4500, 2048, False) == 2048
+    assert bench._prerun_steps(0, 128, False) == 0
+    assert bench._prerun_steps(900, 1536, True) == 0  # --cold-start
