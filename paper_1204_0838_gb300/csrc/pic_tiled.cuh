@@ -126,16 +126,28 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom
   // Lane order.  Particles that share a cell sit next to each other in a
   // tile's list (loading and the stable scatter keep their order), so with
   // consecutive lanes the deposit atomics of a warp often hit an address
-  // twice.  Here each chunk of 64 particles goes to a pair of warps, the even
-  // ones to the first and the odd ones to the second: neighbours in the list
-  // never share a warp, while a warp's lanes still cover a run of
-  // neighbouring cells, as the gather's shared-memory reads prefer (measured:
-  // faster than both consecutive lanes and lanes spread over the whole tile).
-  // blockDim.x is 256 (four warp pairs).
+  // twice.  FP32: each chunk of 64 particles goes to a pair of warps, the
+  // even ones to the first and the odd ones to the second, so that list
+  // neighbours never share a warp while a warp's lanes still cover a run of
+  // neighbouring cells, as the gather's shared-memory reads prefer.  FP64:
+  // the lanes of a warp take particles mrow apart in the list, which also
+  // spreads the many particles of a dense cell (bubble walls) over warps.
+  // Measured on a run's state, each better than the other order for its
+  // precision.  blockDim.x is 256 (four warp pairs).
+  constexpr bool kSpread = sizeof(T) == 8;
   const int ntile = pend - pbeg;
-  for (int base = 0; base < ntile; base += blockDim.x) {
+  const int mrow = (ntile + 31) >> 5;
+  const int nloop = kSpread ? 32 * mrow : ntile;
+  for (int base = 0; base < nloop; base += blockDim.x) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pi = pbeg + base + ((w >> 1) << 6) + (lane << 1) + (w & 1);  // pi >= pend: no particle
+    int pi;  // pi >= pend: no particle
+    if (kSpread) {
+      const int kk = base + threadIdx.x;
+      const int loc = lane * mrow + (kk >> 5);
+      pi = (kk < nloop && loc < ntile) ? pbeg + loc : pend;
+    } else {
+      pi = pbeg + base + ((w >> 1) << 6) + (lane << 1) + (w & 1);
+    }
     int key = -2;
     if (pi < pend) {
       const int cell = p.cell[pi];
