@@ -485,6 +485,98 @@ def test_in_box_focused_laser_is_divergence_free():
     assert 1.5 < np.abs(s.field(O.EY)).max() < 2.0 + 1e-9
 
 
+# ---------------------------------------------------------------------------
+# The focused pulse of Sec. 3.1 against the closed-form Gaussian beam: the
+# fundamental mode of waist w0 has the Rayleigh length z_R = k w0^2 / 2; at
+# x - x_f = +-z_R its on-axis amplitude is a0 / sqrt(2) and its 1/e radius
+# sqrt(2) w0; through focus the on-axis phase runs ahead of a plane wave by the
+# Gouy phase atan((x - x_f) / z_R) (pi/4 at z_R: phase velocity above c); the
+# wavefront radius is R = z + z_R^2 / z, so at r = w0 the phase differs from
+# the axis by -k w0^2 / (2 R) = -/+ 1/2 rad at +-z_R (before focus the
+# off-axis field leads: the beam converges).  Amplitude and phase are taken
+# from samples of the oracle's field over one period (a pulse long enough that
+# its envelope is flat there).
+# ---------------------------------------------------------------------------
+def _beam_sim(w0):
+    s = _sim(16, 8, 8, periodic_x=True)
+    s.add_laser(1.0, w0, 1e6 * LAM / C0, LAM, x_focus=0.0, t_peak=0.0, mode="in_box")
+    inf = s.info()
+    return s, inf
+
+
+def _amp_phase(s, inf, xi, r):
+    """Amplitude and phase of Ey at distance xi (normalised) from focus and
+    radius r from the axis, the phase taken against the plane wave
+    sin(k (t - t_peak) - k (x - x_f)) that moves at c (k = 1 here)."""
+    yc, zc = 0.5 * 8 * inf["dy"], 0.5 * 8 * inf["dz"]
+    tau = np.linspace(0.0, 2 * np.pi, 64, endpoint=False)
+    ey = np.array([s.laser_ey(xi, yc + r, zc, xi + t) for t in tau])
+    a = 2 * np.mean(ey * np.sin(tau))
+    b = 2 * np.mean(ey * np.cos(tau))
+    return math.hypot(a, b), math.atan2(b, a)
+
+
+def test_focused_beam_closed_forms_at_focus_and_rayleigh_length():
+    w0_si = 2.0 * LAM
+    s, inf = _beam_sim(w0_si)
+    w0 = w0_si * 2 * np.pi / LAM
+    zr = 0.5 * w0 ** 2
+    a_f, ph_f = _amp_phase(s, inf, 0.0, 0.0)
+    assert abs(a_f - 1.0) < 1e-9 and abs(ph_f) < 1e-9
+    for sgn in (-1.0, 1.0):
+        a_r, ph_r = _amp_phase(s, inf, sgn * zr, 0.0)
+        assert abs(a_r - 1 / math.sqrt(2)) < 1e-9          # a0 w0 / w(z_R)
+        assert abs(ph_r - sgn * math.pi / 4) < 1e-9       # Gouy phase
+        a_w, _ = _amp_phase(s, inf, sgn * zr, math.sqrt(2) * w0)
+        assert abs(a_w / a_r - math.exp(-1)) < 1e-9       # 1/e radius sqrt(2) w0
+        _, ph_w0 = _amp_phase(s, inf, sgn * zr, w0)
+        assert abs((ph_w0 - ph_r) - (-sgn * 0.5)) < 1e-9  # -k w0^2 / (2 R(+-z_R))
+    a_w, _ = _amp_phase(s, inf, 0.0, w0)
+    assert abs(a_w - math.exp(-1)) < 1e-9                 # 1/e radius w0 at focus
+    # the Gouy phase runs monotonically through focus: phase velocity above c
+    ph = [_amp_phase(s, inf, q * zr, 0.0)[1] for q in (-2, -1, -0.5, 0, 0.5, 1, 2)]
+    assert np.all(np.diff(ph) > 0)
+    assert abs(ph[-1] - math.atan(2.0)) < 1e-9
+
+
+@pytest.mark.slow
+def test_focused_pulse_propagates_to_its_focus():
+    """A focused in-box pulse started 1.5 z_R before its focus in a vacuum
+    window moving at c: the field solver carries it through the focus, where
+    its on-axis envelope peaks, with the beam's own Rayleigh length.  A wrong
+    curvature sign, waist law or Rayleigh length in the initial field moves
+    the measured focus by about z_R or more.  Bounds: the transverse cell of
+    lambda0/2 (the paper's) shifts the focus by 0.13 z_R and lengthens z_R by
+    18 % (with lambda0/4: 0.05 z_R and 10 %, the rest being paraxial error at
+    w0 = 1.5 lambda0)."""
+    from scipy.signal import hilbert
+    nx, ny, nz = 64, 32, 32
+    dx = LAM / 8
+    w0 = 1.5 * LAM
+    zr_si = math.pi * w0 ** 2 / LAM
+    xc0 = -1.5 * zr_si                   # envelope centre at t = 0, mid-window
+    s = O.Sim(nx, ny, nz, dx, LAM / 2, LAM / 2, LAM, x0=xc0 - nx * dx / 2, periodic_x=False,
+              window=(1.0, 0.0))
+    s.add_laser(1.0, w0, 2 * LAM / C0, LAM, x_focus=0.0, t_peak=-xc0 / C0)
+    nsteps = int(round(3 * zr_si / dx))
+    xs, amps = [], []
+    for n in range(nsteps + 1):
+        if n % 2 == 0:
+            ey = s.field(O.EY)
+            axis = 0.5 * (ey[:, ny // 2 - 1, nz // 2] + ey[:, ny // 2, nz // 2])
+            amps.append(np.abs(hilbert(axis)).max())
+            xs.append(xc0 + n * dx)
+        s.step(1)
+    assert s.info()["shifts"] == nsteps + 1
+    xs, amps = np.array(xs), np.array(amps)
+    f = lambda x, A, x1, z1: A / np.sqrt(1 + ((x - x1) / z1) ** 2)
+    (A, x1, z1), _ = curve_fit(f, xs, amps, p0=[1.0, 0.0, zr_si])
+    assert abs(x1) < 0.3 * zr_si
+    assert abs(z1 / zr_si - 1) < 0.3
+    assert abs(A - 1) < 0.1
+    assert amps[0] < 0.65 and amps[-1] < 0.7 and amps.max() > 0.9
+
+
 def test_window_injection_and_absorption():
     nx, ny, nz, ppc = 32, 4, 4, 2
     dx = LAM / 16
