@@ -39,9 +39,8 @@ FLOP_PER_PARTICLE = 1613
 BYTES_PER_PARTICLE = {"fp64": 112, "fp32": 60}  # SoA record read once, written once
 # DRAM bytes (read + write) per particle of k_push_tiled, from one ncu capture
 # of the current kernel on a 256x128x128 window in a run's own state (run for
-# 256 steps past a load at rest), FP64 8x8x16 and FP32 8x8x8 tiles
-# (profiles/k_push_tiled_small_fp64_fp32.md); traffic per launch scales with
-# the particles processed.
+# 256 steps past a load at rest), FP64 8x8x16 and FP32 8x8x8 tiles; traffic
+# per launch scales with the particles processed.
 NCU_TRAFFIC_PER_PARTICLE = {"fp64": 1325.259776e6 / 8336282, "fp32": 699.216640e6 / 8336282}
 
 

@@ -80,6 +80,15 @@ extern "C" {
                                    p_x / (m c) in [a->p_min, a->p_max), C (Fig. 3)     */
 #define PIC_DIAG_DENSITY_XY 6   /* len >= nx * ny: electron density in the z = nz/2 cell
                                    plane, [i][j], units of n_c (Fig. 2)               */
+#define PIC_DIAG_DIVE_RESIDUAL 7 /* len >= 1: Gauss-law residual max |div E - rho| / max |rho_e|
+                                   over the nodes, dimensionless (Sec. 2: the charge-
+                                   conserving deposit keeps div E - rho fixed in time).
+                                   rho = the electrons' cubic node density plus the
+                                   immobile ions (Sec. 1), the frozen negative of the
+                                   electrons as loaded; div E is the standard Yee
+                                   divergence at the nodes.  len >= 3 adds out[1] =
+                                   max |div E - rho| and out[2] = max |rho_e| in C/m^3.
+                                   Uses 16 bytes of device scratch per cell.         */
 #define PIC_FLAG_TRACK_IDS 1u   /* carry a 32-bit id per particle (tests, tracking) */
 
 /* Optional device-memory hooks (e.g. a framework's caching allocator).
@@ -205,8 +214,16 @@ int pic_add_species(pic_t* h, const pic_profile* n, int ppc, int spline_order, d
 int pic_add_laser(pic_t* h, double a0, double waist, double duration_fwhm, double lambda0,
                   const pic_laser_opts* opts);
 
-/* Advance n steps (asynchronous on the handle's stream; the device error word
- * is read back, and the stream synchronised, before returning). */
+/* Advance n steps of the explicit PIC cycle (Sec. 1): per step, gather E and B
+ * to every macroparticle with its cubic shape, Boris-push it and move it,
+ * deposit its current with the charge-conserving Esirkepov scheme, then
+ * update B and E by Eq. (perfDispMaxwell) (Sec. 2: the curl smoothed
+ * transversely, c dt = dx), and with a window move the box one cell when the
+ * window accumulator crosses a cell, injecting the plasma of the new front
+ * slab (Sec. 1).  Asynchronous on the handle's stream; the device error word
+ * is read back, and the stream synchronised, before returning.  Errors:
+ * PIC_ERR_ARG (n < 0), PIC_ERR_STATE (a batched handle), PIC_ERR_CAPACITY,
+ * PIC_ERR_NUMERIC (a non-finite momentum), PIC_ERR_CUDA. */
 int pic_step(pic_t* h, int n);
 
 /* Diagnostics into a caller-owned host buffer of len doubles, SI units
@@ -266,9 +283,10 @@ int pic_destroy(pic_t* h);
  * library until it is unloaded).  It calls no cudaMalloc, cudaFree or other
  * allocating routine.  Results longer than PIC_NOALLOC_MAX_LEN values (a
  * lineout of nx > 65536 cells, a spectrum of more bins) return PIC_ERR_ARG.
- * The first call made with a given device current looks up the array's
- * device address (cudaGetSymbolAddress) once for that device; make that first
- * call before any stream capture.  All calls share the array: each call
+ * pic_create looks up the array's device address (cudaGetSymbolAddress) on
+ * the device current at creation, the handle's device, and keeps it in the
+ * handle; each call makes that device current while it runs and synchronises
+ * the handle's stream before returning.  All calls share the array: each call
  * clears the part it uses, and calls that overlap on the GPU race on it. */
 #define PIC_NOALLOC_MAX_LEN 65536
 int pic_diag_noalloc(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* a);

@@ -1025,6 +1025,10 @@ int or_diag(or_sim* s, int kind, double* out, size_t len, double p0, double p1) 
         if (fabs(rho[q]) > rmax) rmax = fabs(rho[q]);
       }
       out[0] = rmax > 0 ? emax / rmax : emax;
+      if (len >= 3) { /* the two maxima themselves, C/m^3 */
+        out[1] = emax * OC_QE * nc;
+        out[2] = rmax * OC_QE * nc;
+      }
       free(div);
       free(rho);
       return 0;

@@ -15,18 +15,13 @@
 #include <vector>
 
 #include "../../include/pic.h"
-#include "pic_tiled.cuh"
+#include "pic_host.h"
 #include "pic_runtime.h"
+#include "pic_tiled.cuh"
 
 using namespace pic;
 
 namespace {
-
-constexpr double kC = 299792458.0;
-constexpr double kQe = 1.602176634e-19;
-constexpr double kMe = 9.1093837015e-31;
-constexpr double kEps0 = 8.8541878128e-12;
-constexpr double kPi = 3.14159265358979323846;
 
 int fail(pic_t* h, int code, const std::string& msg) {
   if (h) h->err = msg;
@@ -71,21 +66,7 @@ dim3 e_update_grid(const pic_t* h) {
   return dim3((h->nz + b - 1) / b, h->ny, h->nx);
 }
 
-int grid_for(long long n, int per_block = 256, int cap = 152 * 32) {
-  long long b = (n + per_block - 1) / per_block;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (int)b;
-}
-
-// Launch accounting and optional per-group timing.
-enum { G_PUSH = 0, G_FIELD = 1, G_PART = 2, G_OTHER = 3 };
-
-inline void counted(pic_t* h, int group, int n = 1) {
-  h->launches[group] += n;
-  h->kernels += n;
-}
-
+// Optional per-group timing.
 cudaEvent_t take_event(pic_t* h) {
   if (!h->ev_pool.empty()) {
     cudaEvent_t e = h->ev_pool.back();
@@ -124,25 +105,6 @@ struct GroupTimer {
     h->ev_pairs[group].push_back({a, b});
   }
 };
-
-template <typename T>
-Geom<T> geom(const pic_t* h) {
-  Geom<T> g;
-  g.nx = h->nx;
-  g.ny = h->ny;
-  g.nz = h->nz;
-  g.origin = h->origin;
-  g.periodic_x = h->periodic_x;
-  g.nyz = h->ny * h->nz;
-  g.dt = (T)h->dt;
-  g.dx = (T)h->dx;
-  g.dy = (T)h->dy;
-  g.dz = (T)h->dz;
-  g.dyn = nullptr;
-  g.gate = 0;
-  g.pml = h->pml;
-  return g;
-}
 
 // Memory variables and coefficients of the absorbing layers (L = 0: none).
 template <typename T>
@@ -197,27 +159,6 @@ Smooth<T> smooth(const pic_t* h) {
     s.g[a] = (T)h->sm_g[a];
   }
   return s;
-}
-
-template <typename T>
-Fields<T> fields(const pic_t* h) {
-  Fields<T> f;
-  for (int c = 0; c < NCOMP; ++c) f.c[c] = (T*)h->fields + (size_t)c * h->ncell;
-  return f;
-}
-
-template <typename T>
-Parts<T> parts(const pic_t* h, int b) {
-  const PartBuf& pb = h->pb[b];
-  Parts<T> p;
-  p.cell = pb.cell;
-  for (int d = 0; d < 3; ++d) {
-    p.o[d] = (T*)pb.o[d];
-    p.u[d] = (T*)pb.u[d];
-  }
-  p.w = (T*)pb.w;
-  p.id = pb.id;
-  return p;
 }
 
 size_t esize(const pic_t* h) { return h->precision == PIC_FP64 ? 8 : 4; }
@@ -355,19 +296,6 @@ int load_cells(pic_t* h, int lo, int hi) {
 }
 
 template <typename T>
-int compact(pic_t* h) {
-  const int nb = 1 - h->cur;
-  CK(h, cudaMemsetAsync(h->d_ctrl + nb, 0, sizeof(int), h->stream));
-  GroupTimer tm(h, G_PART);
-  counted(h, G_PART);
-  k_compact<T><<<grid_for(h->capacity, 256, 152 * 16), 256, 0, h->stream>>>(
-      geom<T>(h), parts<T>(h, h->cur), h->d_ctrl + h->cur, parts<T>(h, nb), h->d_ctrl + nb, x_lo(h), x_hi(h));
-  CK(h, cudaGetLastError());
-  h->cur = nb;
-  return PIC_OK;
-}
-
-template <typename T>
 int hard_source(pic_t* h, double t) {
   const Laser L = laser_params(h);
   const double xplane = h->x0 + (double)h->shifts * h->dx;
@@ -447,7 +375,7 @@ int curl_only(pic_t* h, int i0, int ni) {
 // Counting sort of the current buffer by tile into the other buffer.
 template <typename T>
 int resort_all(pic_t* h) {
-  if (!h->tiled || h->capacity == 0) return PIC_OK;
+  if (h->capacity == 0) return PIC_OK;
   const int nb = 1 - h->cur;
   const Tiles tl = h->tiles;
   GroupTimer tm(h, G_PART);
@@ -594,49 +522,6 @@ int step_tiled(pic_t* h) {
   return PIC_OK;
 }
 
-// One step with the unsorted one-thread-per-particle kernel and stream
-// compaction (kept for comparison; selected with PIC_KERNEL=simple).
-template <typename T>
-int step_simple(pic_t* h) {
-  const size_t n = h->ncell;
-  Fields<T> f = fields<T>(h);
-  const double t_old = (double)h->step * h->dt, t_new = (double)(h->step + 1) * h->dt;
-  double frac_new;
-  const int shift = window_due(h, t_old, t_new, &frac_new);
-  CK(h, cudaMemsetAsync(f.c[JX], 0, 3 * n * sizeof(T), h->stream));
-  if (h->capacity > 0) {
-    GroupTimer tm(h, G_PUSH);
-    counted(h, G_PUSH);
-    const T hq = (T)(h->q * h->dt / (2.0 * h->m));
-    k_push_deposit<T><<<grid_for(h->capacity, 256, 152 * 16), 256, 0, h->stream>>>(
-        geom<T>(h), f, parts<T>(h, h->cur), h->d_ctrl + h->cur, hq, (T)h->q, h->d_pushed);
-  }
-  int rc = field_first_half<T>(h);
-  if (rc) return rc;
-  h->step += 1;
-  if (h->laser_mode == PIC_LASER_HARD_SOURCE) {
-    rc = hard_source<T>(h, t_new);
-    if (rc) return rc;
-  }
-  rc = field_second_half<T>(h);
-  if (rc) return rc;
-  h->win_frac = frac_new;
-  if (shift) {
-    h->win_frac -= 1.0;
-    const int old_origin = h->origin;
-    h->origin = (h->origin + 1) % h->nx;
-    h->shifts += 1;
-    rc = after_shift_fields<T>(h, old_origin);
-    if (rc) return rc;
-  }
-  if (h->capacity > 0 && !h->periodic_x) {
-    rc = compact<T>(h);
-    if (rc) return rc;
-  }
-  if (shift && h->has_species) return load_cells<T>(h, x_hi(h), x_hi(h));
-  return PIC_OK;
-}
-
 template <typename T>
 int step_impl(pic_t* h, int nsteps) {
   if (h->need_sort && nsteps > 0) {
@@ -645,7 +530,7 @@ int step_impl(pic_t* h, int nsteps) {
     h->need_sort = false;
   }
   for (int it = 0; it < nsteps; ++it) {
-    int rc = h->tiled ? step_tiled<T>(h) : step_simple<T>(h);
+    int rc = step_tiled<T>(h);
     if (rc) return rc;
   }
   return PIC_OK;
@@ -683,15 +568,58 @@ int check_device_error(pic_t* h) {
   return PIC_OK;
 }
 
+// Gauss-law residual: out[0] = max |div E - rho| / max |rho_e| over the nodes
+// (rho = electrons plus immobile ions; max |div E - rho| itself when there is
+// no electron charge); with len >= 3 also out[1] = max |div E - rho| and
+// out[2] = max |rho_e|, in C/m^3.  Scratch: [2 words][rho_e][rho_i].
+template <typename T>
+int gauss_residual(pic_t* h, double* out, size_t len) {
+  const Geom<T> g = geom<T>(h);
+  double* rho_e = h->d_diag + 2;
+  double* rho_i = rho_e + h->ncell;
+  const double dV = h->dx * h->dy * h->dz;
+  if (h->capacity > 0) {
+    counted(h, G_OTHER);
+    k_rho_particles<T><<<grid_for(h->capacity, 256, 152 * 8), 256, 0, h->stream>>>(
+        g, parts<T>(h, h->cur), h->d_ctrl + h->cur, h->q / dV, rho_e);
+  }
+  if (h->has_species) {
+    // every lab cell loaded so far: the set-up load and one front slab per shift
+    const int lo = h->periodic_x ? 0 : (int)std::max<long long>(h->ion_lab_lo - h->shifts, -2);
+    const int hi = x_hi(h);
+    if (lo <= hi) {
+      const LoadSpec L = load_spec(h, lo, hi);
+      counted(h, G_OTHER);
+      k_rho_ions<T><<<grid_for((long long)(hi - lo + 1) * h->ny * h->nz * h->ppc, 256, 152 * 8), 256, 0,
+                      h->stream>>>(g, L, -h->q / dV, rho_i);
+    }
+  }
+  counted(h, G_OTHER);
+  k_gauss_residual<T><<<grid_for((long long)h->ncell, 256, 152 * 8), 256, 0, h->stream>>>(
+      g, fields<T>(h), rho_e, rho_i, 1.0 / h->dx, 1.0 / h->dy, 1.0 / h->dz, (unsigned long long*)h->d_diag);
+  CK(h, cudaGetLastError());
+  double m[2];
+  CK(h, cudaMemcpyAsync(m, h->d_diag, sizeof(m), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  const double qsi = kQe * diag_units(h).nc;  // e n_c: C/m^3 per normalised charge density
+  out[0] = m[1] > 0 ? m[0] / m[1] : m[0];
+  if (len >= 3) {
+    out[1] = m[0] * qsi;
+    out[2] = m[1] * qsi;
+  }
+  for (size_t i = 0; i < std::min<size_t>(len, 3); ++i)
+    if (!std::isfinite(out[i])) return fail(h, PIC_ERR_NUMERIC, "diagnostic is not finite");
+  return PIC_OK;
+}
+
 template <typename T>
 int diag_impl(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* a) {
-  const double omega0 = h->omega0;
-  const double Eunit = kMe * kC * omega0 / kQe;
-  const double Lunit = kC / omega0;
-  const double nc = kEps0 * kMe * omega0 * omega0 / (kQe * kQe);
-  const double Qunit = kQe * nc * Lunit * Lunit * Lunit;
-  const double mc2 = kMe * kC * kC / (kQe * 1e6) * h->m;
+  const DiagUnits un = diag_units(h);
   size_t need = std::max<size_t>(std::max<size_t>(len, 11), (size_t)h->nx * h->ny);
+  if (kind == PIC_DIAG_DIVE_RESIDUAL) {
+    if (len < 1) return fail(h, PIC_ERR_ARG, "len < 1");
+    need = std::max(need, 2 + 2 * h->ncell);
+  }
   if (need > h->diag_cap) {
     dfree(h, h->d_diag);
     h->d_diag = (double*)dalloc(h, need * sizeof(double));
@@ -702,39 +630,15 @@ int diag_impl(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* 
     h->diag_cap = need;
   }
   CK(h, cudaMemsetAsync(h->d_diag, 0, need * sizeof(double), h->stream));
+  if (kind == PIC_DIAG_DIVE_RESIDUAL) return gauss_residual<T>(h, out, len);
   const Geom<T> g = geom<T>(h);
-  Fields<T> f = fields<T>(h);
   double scale = 1.0;
   size_t nout = 1;
-  switch (kind) {
-    case PIC_DIAG_EX_LINEOUT:
-      if (len < (size_t)h->nx) return fail(h, PIC_ERR_ARG, "lineout needs len >= nx");
-      counted(h, G_OTHER);
-      k_lineout<T><<<grid_for(h->nx), 256, 0, h->stream>>>(g, f.c[EX], h->d_diag);
-      scale = Eunit;
-      nout = h->nx;
-      break;
-    case PIC_DIAG_FIELD_ENERGY:
-      if (len < 1) return fail(h, PIC_ERR_ARG, "len < 1");
-      counted(h, G_OTHER);
-      k_field_energy<T><<<grid_for(h->ncell, 256, 152 * 8), 256, 0, h->stream>>>(g, f, h->d_diag);
-      scale = 0.5 * h->dx * h->dy * h->dz * kEps0 * Eunit * Eunit * Lunit * Lunit * Lunit;
-      break;
-    case PIC_DIAG_CHARGE:
-    case PIC_DIAG_SPECTRUM: {
-      if (len < 1) return fail(h, PIC_ERR_ARG, "len < 1");
-      const bool spec = kind == PIC_DIAG_SPECTRUM;
-      if (!a) return fail(h, PIC_ERR_ARG, "diagnostic arguments required");
-      if (spec && !(a->e_max > a->e_min)) return fail(h, PIC_ERR_ARG, "e_max <= e_min");
-      if (h->capacity > 0) counted(h, G_OTHER);
-      if (h->capacity > 0)
-        k_particle_diag<T><<<grid_for(h->capacity, 256, 152 * 8), 256, 0, h->stream>>>(
-            parts<T>(h, h->cur), h->d_ctrl + h->cur, spec ? 1 : 0, a->gamma_min, mc2, a->e_min, a->e_max,
-            (int)len, h->d_diag);
-      scale = std::fabs(h->q) * Qunit;
-      nout = spec ? len : 1;
-      break;
-    }
+  if (is_basic_diag(kind)) {
+    int rc = basic_diag_check(h, kind, len, a, &nout, &scale, &h->err);
+    if (rc) return rc;
+    basic_diag_launch<T>(h, kind, len, a, h->d_diag);
+  } else switch (kind) {
     case PIC_DIAG_EMITTANCE: {
       if (len < 2) return fail(h, PIC_ERR_ARG, "emittance needs len >= 2");
       if (!a) return fail(h, PIC_ERR_ARG, "diagnostic arguments required");
@@ -758,7 +662,7 @@ int diag_impl(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* 
           const double det = var_u * var_r - cov * cov;
           e = det > 0 ? std::sqrt(det) : 0.0;
         }
-        out[ax] = e * Lunit;  // normalised length -> metres (u is dimensionless)
+        out[ax] = e * un.L;  // normalised length -> metres (u is dimensionless)
         if (!std::isfinite(out[ax])) return fail(h, PIC_ERR_NUMERIC, "diagnostic is not finite");
       }
       return PIC_OK;
@@ -771,7 +675,7 @@ int diag_impl(pic_t* h, int kind, double* out, size_t len, const pic_diag_args* 
         k_phase_x_px<T><<<grid_for(h->capacity, 256, 152 * 8), 256, 0, h->stream>>>(
             g, parts<T>(h, h->cur), h->d_ctrl + h->cur, a->p_min, a->p_max, (int)(len / h->nx), h->d_diag);
       }
-      scale = std::fabs(h->q) * Qunit;
+      scale = std::fabs(h->q) * un.Q;
       nout = len;
       break;
     }
@@ -874,8 +778,6 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
     h->win_t0 = w->t_start * h->omega0;
   }
   {
-    const char* kern = std::getenv("PIC_KERNEL");
-    h->tiled = !(kern && std::strcmp(kern, "simple") == 0) || h->pml > 0;  // the simple path has no layers
     int t3[3] = {8, 8, 8};
     const char* ts = std::getenv("PIC_TILE");
     if (ts) std::sscanf(ts, "%d,%d,%d", &t3[0], &t3[1], &t3[2]);
@@ -886,9 +788,10 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
     tl.ty = t3[1];
     tl.tz = t3[2];
     // keep the shared-memory tile within the 227 KB a CTA may use
-    const size_t es = h->precision == PIC_FP64 ? 8 : 4;
-    while (es * (6 * (size_t)(tl.tx + 4) * (tl.ty + 4) * (tl.tz + 4) + 3 * (size_t)(tl.tx + 5) * (tl.ty + 5) * (tl.tz + 5)) >
-           227 * 1024) {
+    auto smem = [&]() {
+      return h->precision == PIC_FP64 ? tiled_smem_bytes<double>(tl) : tiled_smem_bytes<float>(tl);
+    };
+    while (smem() > 227 * 1024) {
       if (tl.tx >= tl.ty && tl.tx >= tl.tz) tl.tx /= 2;
       else if (tl.ty >= tl.tz) tl.ty /= 2;
       else tl.tz /= 2;
@@ -899,11 +802,15 @@ int pic_create(const pic_grid* g, double dt, const pic_window* w, pic_t** out) {
     tl.n = tl.ntx * tl.nty * tl.ntz;
   }
   set_coefficients(h);
-  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     delete h;
     return PIC_ERR_CUDA;
   }
+  // pic_diag_noalloc's scratch address on this device; a failure here only
+  // disables that call (it then returns PIC_ERR_CUDA)
+  if (noalloc_attach(h) != cudaSuccess) cudaGetLastError();
   h->stream = h->own_stream;
   h->fields = dalloc(h, NCOMP * h->ncell * esize(h));
   h->curl = dalloc(h, 3 * h->ncell * esize(h));
@@ -1022,6 +929,7 @@ int pic_add_species(pic_t* h, const pic_profile* n, int ppc, int spline_order, d
   int rc = ensure_particles(h, cap);
   if (rc) return rc;
   h->has_species = true;
+  h->ion_lab_lo = h->shifts + x_lo(h);
   rc = h->precision == PIC_FP64 ? load_cells<double>(h, x_lo(h), x_hi(h)) : load_cells<float>(h, x_lo(h), x_hi(h));
   if (rc) return rc;
   h->need_sort = true;
@@ -1729,7 +1637,6 @@ int autotune_impl(pic_t* h, int steps, const char* cache_path, int out3[3], doub
 extern "C" int pic_autotune(pic_t* h, int steps, const char* cache_path, int* tile_out, double* ms_out) {
   if (!h || steps < 1) return PIC_ERR_ARG;
   if (h->batched) return fail(h, PIC_ERR_STATE, "handle is part of a batch");
-  if (!h->tiled) return fail(h, PIC_ERR_STATE, "autotuning needs the tiled particle path");
   if (!cache_path) cache_path = std::getenv("PIC_AUTOTUNE_CACHE");
   int t3[3];
   double ms = 0.0;
@@ -1922,7 +1829,7 @@ int pic_batch_create(int n, pic_t* const* sims, pic_batch_t** out) {
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!sims[i]) return PIC_ERR_ARG;
-    if (sims[i]->precision != PIC_FP32 || sims[i]->batched || !sims[i]->tiled) return PIC_ERR_STATE;
+    if (sims[i]->precision != PIC_FP32 || sims[i]->batched) return PIC_ERR_STATE;
     if (sims[i]->laser_mode == PIC_LASER_HARD_SOURCE) return PIC_ERR_STATE;  // time-driven source: host path only
     for (int j = 0; j < i; ++j)
       if (sims[j] == sims[i]) return PIC_ERR_ARG;

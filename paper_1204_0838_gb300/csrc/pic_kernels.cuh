@@ -363,197 +363,6 @@ __global__ void __launch_bounds__(256) k_curl_tiled(Geom<T> g, Smooth<T> S, Fiel
 }
 
 // ---------------------------------------------------------------------------
-// Gather + Boris push + position update + Esirkepov deposit, one thread per
-// particle; fields read from global memory, J accumulated with atomics.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T gather_comp(const T* __restrict__ F, const Geom<T>& g, const int* ix, const int* iy,
-                                         const int* iz, int shx, int shy, int shz, const T* wx, const T* wy,
-                                         const T* wz) {
-  T acc = T(0);
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const size_t sa = (size_t)ix[a + shx] * g.nyz;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const size_t sb = sa + (size_t)iy[b + shy] * g.nz;
-      const T wab = wx[a] * wy[b];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc += __ldg(F + sb + iz[c + shz]) * wab * wz[c];
-    }
-  }
-  return acc;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_push_deposit(Geom<T> g, Fields<T> f, Parts<T> p,
-                                                     const int* __restrict__ d_np, T h /* q dt / 2m */,
-                                                     T q, unsigned long long* pushed) {
-  const int n = *d_np;
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(pushed, (unsigned long long)n);
-  const int N[3] = {g.nx, g.ny, g.nz};
-  const T dinv[3] = {T(1) / g.dx, T(1) / g.dy, T(1) / g.dz};
-  const T jc[3] = {T(-1) / (g.dt * g.dy * g.dz), T(-1) / (g.dt * g.dx * g.dz), T(-1) / (g.dt * g.dx * g.dy)};
-  for (int pi = blockIdx.x * blockDim.x + threadIdx.x; pi < n; pi += gridDim.x * blockDim.x) {
-    const int cell = p.cell[pi];
-    int c0[3];
-    c0[0] = cell / g.nyz;
-    const int rem = cell - c0[0] * g.nyz;
-    c0[1] = rem / g.nz;
-    c0[2] = rem - c0[1] * g.nz;
-    T o0[3], u[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      o0[d] = p.o[d][pi];
-      u[d] = p.u[d][pi];
-    }
-    // cubic weights: node-centred (nodes c-1..c+2) and half-centred
-    // (half nodes c-2..c+1 for offset < 1/2, else c-1..c+2)
-    T wn[3][4], wh[3][4];
-    int hs[3];  // index shift of the half-centred window inside idx5
-    int idx5[3][5];  // wrapped storage indices of nodes c-2 .. c+2
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      bspline3(o0[d], wn[d]);
-      const bool lo = o0[d] < T(0.5);
-      bspline3(lo ? o0[d] + T(0.5) : o0[d] - T(0.5), wh[d]);
-      hs[d] = lo ? 0 : 1;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) idx5[d][m] = wrapi(c0[d] - 2 + m, N[d]);
-    }
-    T E[3], B[3];
-    E[0] = gather_comp(f.c[EX], g, idx5[0], idx5[1], idx5[2], hs[0], 1, 1, wh[0], wn[1], wn[2]);
-    E[1] = gather_comp(f.c[EY], g, idx5[0], idx5[1], idx5[2], 1, hs[1], 1, wn[0], wh[1], wn[2]);
-    E[2] = gather_comp(f.c[EZ], g, idx5[0], idx5[1], idx5[2], 1, 1, hs[2], wn[0], wn[1], wh[2]);
-    B[0] = gather_comp(f.c[BX], g, idx5[0], idx5[1], idx5[2], 1, hs[1], hs[2], wn[0], wh[1], wh[2]);
-    B[1] = gather_comp(f.c[BY], g, idx5[0], idx5[1], idx5[2], hs[0], 1, hs[2], wh[0], wn[1], wh[2]);
-    B[2] = gather_comp(f.c[BZ], g, idx5[0], idx5[1], idx5[2], hs[0], hs[1], 1, wh[0], wh[1], wn[2]);
-
-    // relativistic Boris push
-    T um[3], t[3], sv[3], up[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) um[d] = u[d] + h * E[d];
-    const T gm = sqrt(T(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) t[d] = h * B[d] / gm;
-    const T t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) sv[d] = T(2) * t[d] / (T(1) + t2);
-    const T ux = um[0] + (um[1] * t[2] - um[2] * t[1]);
-    const T uy = um[1] + (um[2] * t[0] - um[0] * t[2]);
-    const T uz = um[2] + (um[0] * t[1] - um[1] * t[0]);
-    up[0] = um[0] + (uy * sv[2] - uz * sv[1]);
-    up[1] = um[1] + (uz * sv[0] - ux * sv[2]);
-    up[2] = um[2] + (ux * sv[1] - uy * sv[0]);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) u[d] = up[d] + h * E[d];
-    const T gam = sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-
-    // position update in cell + offset form; |move| < 1 cell per axis
-    T o1[3];
-    int dc[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T o = o0[d] + g.dt * u[d] / gam * dinv[d];
-      int k = 0;
-      if (o < T(0)) {
-        o += T(1);
-        k = -1;
-      } else if (o >= T(1)) {
-        o -= T(1);
-        k = 1;
-      }
-      if (o >= T(1)) {  // o was a tiny negative number that rounded to 1
-        o = T(0);
-        k += 1;
-      }
-      o1[d] = o;
-      dc[d] = k;
-    }
-
-    // Esirkepov deposit on a 5-node window per axis starting at c0-1+min(dc,0)
-    T S0[3][5], DS[3][5];
-    int ws[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T w0[4], w1[4];
-      bspline3(o0[d], w0);
-      bspline3(o1[d], w1);
-      const int p0 = dc[d] < 0 ? 1 : 0;
-      const int p1 = dc[d] > 0 ? 1 : 0;
-      ws[d] = c0[d] - 1 + (dc[d] < 0 ? -1 : 0);
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        // S0 occupies window nodes p0..p0+3, S1 nodes p1..p1+3 (p0, p1 in {0,1})
-        const T a0 = p0 ? (m > 0 ? w0[m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? w0[m < 4 ? m : 3] : T(0));
-        const T a1 = p1 ? (m > 0 ? w1[m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? w1[m < 4 ? m : 3] : T(0));
-        S0[d][m] = a0;
-        DS[d][m] = a1 - a0;
-      }
-    }
-    const T qw = q * p.w[pi];
-    int jx[5], jy[5], jz[5];
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      jx[m] = wrapi(ws[0] + m, g.nx);
-      jy[m] = wrapi(ws[1] + m, g.ny);
-      jz[m] = wrapi(ws[2] + m, g.nz);
-    }
-    const T third = T(1) / T(3);
-    {  // Jx: running sum along x of Wx
-      const T cf = qw * jc[0];
-      for (int b = 0; b < 5; ++b)
-        for (int c = 0; c < 5; ++c) {
-          const T tt = S0[1][b] * S0[2][c] + T(0.5) * DS[1][b] * S0[2][c] + T(0.5) * S0[1][b] * DS[2][c] +
-                       DS[1][b] * DS[2][c] * third;
-          T run = T(0);
-          for (int a = 0; a < 4; ++a) {
-            run += DS[0][a] * tt;
-            if (run != T(0)) atomicAdd(f.c[JX] + (size_t)jx[a] * g.nyz + (size_t)jy[b] * g.nz + jz[c], cf * run);
-          }
-        }
-    }
-    {  // Jy
-      const T cf = qw * jc[1];
-      for (int a = 0; a < 5; ++a)
-        for (int c = 0; c < 5; ++c) {
-          const T tt = S0[0][a] * S0[2][c] + T(0.5) * DS[0][a] * S0[2][c] + T(0.5) * S0[0][a] * DS[2][c] +
-                       DS[0][a] * DS[2][c] * third;
-          T run = T(0);
-          for (int b = 0; b < 4; ++b) {
-            run += DS[1][b] * tt;
-            if (run != T(0)) atomicAdd(f.c[JY] + (size_t)jx[a] * g.nyz + (size_t)jy[b] * g.nz + jz[c], cf * run);
-          }
-        }
-    }
-    {  // Jz
-      const T cf = qw * jc[2];
-      for (int a = 0; a < 5; ++a)
-        for (int b = 0; b < 5; ++b) {
-          const T tt = S0[0][a] * S0[1][b] + T(0.5) * DS[0][a] * S0[1][b] + T(0.5) * S0[0][a] * DS[1][b] +
-                       DS[0][a] * DS[1][b] * third;
-          T run = T(0);
-          for (int c = 0; c < 4; ++c) {
-            run += DS[2][c] * tt;
-            if (run != T(0)) atomicAdd(f.c[JZ] + (size_t)jx[a] * g.nyz + (size_t)jy[b] * g.nz + jz[c], cf * run);
-          }
-        }
-    }
-
-    // store the advanced particle (cell wrapped into the ring / periodic box)
-    const int nx1 = wrapi(c0[0] + dc[0], g.nx);
-    const int ny1 = wrapi(c0[1] + dc[1], g.ny);
-    const int nz1 = wrapi(c0[2] + dc[2], g.nz);
-    p.cell[pi] = nx1 * g.nyz + ny1 * g.nz + nz1;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      p.o[d][pi] = o1[d];
-      p.u[d][pi] = u[d];
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Laser: boundary source on the window's back plane, and in-box start.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -696,37 +505,6 @@ static __global__ void k_clamp_count(int* d_np, int capacity) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && *d_np > capacity) *d_np = capacity;
 }
 
-// Drop particles outside the allowed relative x cells [lo, hi] (open x),
-// compacting into a second buffer with warp-aggregated appends.
-template <typename T>
-__global__ void k_compact(Geom<T> g, Parts<T> src, const int* __restrict__ d_np_src, Parts<T> dst,
-                          int* d_np_dst, int lo, int hi) {
-  const int n = *d_np_src;
-  const int stride = gridDim.x * blockDim.x;
-  for (int q0 = blockIdx.x * blockDim.x; q0 < n; q0 += stride) {
-    const int q = q0 + threadIdx.x;
-    bool keep = false;
-    int cell = 0;
-    if (q < n) {
-      cell = src.cell[q];
-      int rel = cell / g.nyz - g.origin;
-      if (rel < 0) rel += g.nx;
-      keep = rel >= lo && rel <= hi;
-    }
-    const int slot = warp_append(d_np_dst, keep);
-    if (keep) {
-      dst.cell[slot] = cell;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        dst.o[d][slot] = src.o[d][q];
-        dst.u[d][slot] = src.u[d][q];
-      }
-      dst.w[slot] = src.w[q];
-      if (dst.id) dst.id[slot] = src.id[q];
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Diagnostics (FP64 reductions).
 // ---------------------------------------------------------------------------
@@ -829,6 +607,131 @@ __global__ void k_density_xy(Geom<T> g, Parts<T> p, const int* __restrict__ d_np
     int i = cell / g.nyz - g.origin;
     if (i < 0) i += g.nx;
     atomicAdd(out + (size_t)i * g.ny + r / g.nz, (double)p.w[q]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-law residual (Sec. 2: the field update takes its current from the
+// particles' motion, and a charge-conserving deposit keeps div E - rho fixed
+// in time).  rho is the node charge density of the cubic shapes in FP64,
+// window-relative [i][j][k]; the immobile ions (Sec. 1) are the frozen
+// negative of the electrons as loaded, regenerated here from the same
+// counter-based draws (and the same rounding of offsets and weights) as the
+// loading, for every lab cell that has been loaded and can reach a node of
+// the window.  Nodes beyond an open x end or an absorbing-layer grid edge are
+// dropped, periodic axes wrap.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void rho_deposit_cubic(const Geom<T>& g, double* rho, int ci, int cj, int ck,
+                                                  const double o[3], double qd) {
+  double w[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) bspline3(o[d], w[d]);
+  for (int a = 0; a < 4; ++a) {
+    int i = ci - 1 + a;
+    if (g.periodic_x)
+      i = wrapi(i, g.nx);
+    else if (i < 0 || i >= g.nx)
+      continue;
+    for (int b = 0; b < 4; ++b) {
+      int j = cj - 1 + b;
+      if (g.pml) {
+        if (j < 0 || j >= g.ny) continue;
+      } else {
+        j = wrapi(j, g.ny);
+      }
+      for (int c = 0; c < 4; ++c) {
+        int k = ck - 1 + c;
+        if (g.pml) {
+          if (k < 0 || k >= g.nz) continue;
+        } else {
+          k = wrapi(k, g.nz);
+        }
+        atomicAdd(rho + ((size_t)i * g.ny + j) * g.nz + k, qd * w[0][a] * w[1][b] * w[2][c]);
+      }
+    }
+  }
+}
+
+// Electrons: qdv = q / dV (the weight carries the number of electrons).
+template <typename T>
+__global__ void k_rho_particles(Geom<T> g, Parts<T> p, const int* __restrict__ d_np, double qdv, double* rho) {
+  const int n = *d_np;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const int cell = p.cell[q];
+    int ci = cell / g.nyz - g.origin;
+    if (ci < 0) ci += g.nx;
+    const int r = cell - (cell / g.nyz) * g.nyz;
+    const double o[3] = {(double)p.o[0][q], (double)p.o[1][q], (double)p.o[2][q]};
+    rho_deposit_cubic(g, rho, ci, r / g.nz, r % g.nz, o, qdv * (double)p.w[q]);
+  }
+}
+
+// Immobile ions of window-relative cells [L.lo, L.hi] (L.lo may be negative
+// for an open window: those cells still reach nodes 0 and 1): qdv = -q / dV.
+template <typename T>
+__global__ void k_rho_ions(Geom<T> g, LoadSpec L, double qdv, double* rho) {
+  const long long nslot = (long long)(L.hi - L.lo + 1) * g.nyz * L.ppc;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nslot;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int sl = (int)(q % L.ppc);
+    const long long c = q / L.ppc;
+    const int r = (int)(c % g.nyz);
+    const int ci = L.lo + (int)(c / g.nyz);
+    const int j = r / g.nz, k = r - (r / g.nz) * g.nz;
+    const long long lab = L.shifts + ci;
+    const unsigned long long cell = ((unsigned long long)lab * g.ny + j) * g.nz + k;
+    const unsigned long long ctr = (cell * L.ppc + sl) * 3ull;
+    double rr[3], o[3];
+    for (int d = 0; d < 3; ++d) rr[d] = unit_uniform(L.seed, ctr + d);
+    if (L.lattice) {
+      const int sx = sl / (L.ns[1] * L.ns[2]), sy = (sl / L.ns[2]) % L.ns[1], sz = sl % L.ns[2];
+      o[0] = (sx + rr[0]) / L.ns[0];
+      o[1] = (sy + rr[1]) / L.ns[1];
+      o[2] = (sz + rr[2]) / L.ns[2];
+    } else {
+      o[0] = rr[0];
+      o[1] = rr[1];
+      o[2] = rr[2];
+    }
+    const bool inner = j >= L.pml && j < g.ny - L.pml && k >= L.pml && k < g.nz - L.pml;
+    const double n = inner ? profile_at(L.px, L.pn, L.np, L.x0 + ((double)lab + o[0]) * L.dx) : 0.0;
+    if (!(n > 0.0)) continue;
+    double os[3];
+    for (int d = 0; d < 3; ++d) {  // the offsets and weight as the loading stored them
+      T od = (T)o[d];
+      if (od >= T(1)) od = one_below<T>();
+      os[d] = (double)od;
+    }
+    rho_deposit_cubic(g, rho, ci, j, k, os, qdv * (double)(T)(n * L.dVppc));
+  }
+}
+
+// max |div E - rho_e - rho_i| and max |rho_e| over the nodes, as the bit
+// patterns of non-negative doubles (which order like the values) in out[0..1].
+template <typename T>
+__global__ void __launch_bounds__(256) k_gauss_residual(Geom<T> g, Fields<T> f, const double* __restrict__ rho_e,
+                                                        const double* __restrict__ rho_i, double idx, double idy,
+                                                        double idz, unsigned long long* out) {
+  const long long n = (long long)g.nx * g.nyz;
+  double rmax = 0.0, emax = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q / g.nyz), r = (int)(q - (long long)i * g.nyz);
+    const int j = r / g.nz, k = r - (r / g.nz) * g.nz;
+    const int s = slab_of(g, i), sm = slab_of(g, i - 1);
+    const double div = ((double)ld(f.c[EX], g, s, j, k) - (double)ld(f.c[EX], g, sm, j, k)) * idx +
+                       ((double)ld(f.c[EY], g, s, j, k) - (double)ld(f.c[EY], g, s, j - 1, k)) * idy +
+                       ((double)ld(f.c[EZ], g, s, j, k) - (double)ld(f.c[EZ], g, s, j, k - 1)) * idz;
+    rmax = fmax(rmax, fabs(div - rho_e[q] - rho_i[q]));
+    emax = fmax(emax, fabs(rho_e[q]));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    rmax = fmax(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
+    emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, (unsigned long long)__double_as_longlong(rmax));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(emax));
   }
 }
 

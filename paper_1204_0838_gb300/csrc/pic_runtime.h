@@ -49,7 +49,6 @@ struct pic_t {
   void* psi = nullptr;
   void* pml_coef = nullptr;
   // tile-sorted particles
-  bool tiled = true;
   pic::Tiles tiles = {1, 1, 1, 1, 1, 1, 1};
   int* keys = nullptr;      // destination tile per particle
   int* tstart[2] = {nullptr, nullptr};  // tile starts of pb[0], pb[1]
@@ -72,6 +71,7 @@ struct pic_t {
 
   // species (one electron-like species; ions immobile and implicit)
   bool has_species = false;
+  long long ion_lab_lo = 0;  // first lab x cell loaded (the immobile ions start there)
   int ppc = 0, loading = 0, lat[3] = {1, 1, 1};
   double q = 0.0, m = 1.0;
   double* d_prof = nullptr;  // x (normalised) then density (n_c)
@@ -95,7 +95,9 @@ struct pic_t {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pairs[4];
   unsigned long long* d_pushed = nullptr;  // device-side particle-step counter
 
-  // streams, batching, errors
+  // device, streams, batching, errors
+  int device = 0;                       // the CUDA device current at pic_create
+  double* noalloc_scratch = nullptr;    // device address of pic_diag_noalloc's array on that device
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
   bool batched = false;

@@ -21,9 +21,60 @@ __device__ __forceinline__ int tile_of(const Geom<T>& g, const Tiles& tl, int cx
 __host__ __device__ __forceinline__ int stage_n(const Tiles& tl) { return (tl.tx + 4) * (tl.ty + 4) * (tl.tz + 4); }
 __host__ __device__ __forceinline__ int jtile_n(const Tiles& tl) { return (tl.tx + 5) * (tl.ty + 5) * (tl.tz + 5); }
 
+// FP32 particle layout of the push (FP64 keeps its own, see k_push_tiled):
+// - cell rounds: the particles of a tile are taken in rounds, round r holding
+//   the r-th particle of every occupied cell (ranks from a shared-memory cell
+//   histogram), so that the lanes of a warp sit in distinct cells while
+//   consecutive lanes stay on neighbouring cells.  Ranks from kRounds - 1 up
+//   share the last round; the order is built for chunks of up to kOrderChunk
+//   list entries.
+// - fixed-point J tile: the deposit adds each contribution as an exact 64-bit
+//   fixed-point integer split over two 32-bit words with native shared-memory
+//   integer reductions (a float add on shared memory is a load plus a
+//   compare-and-swap loop).  The scale is a power of two 2^s per tile and
+//   component with 2^s <= 2^42 / B, B = |q jc| sum_p w_p over the tile: no
+//   node of the tile can receive more than B in magnitude (each contribution
+//   is bounded by |q w jc|), so the high word stays within 2^30 and the low
+//   word (12 bits per contribution) within 2^32 for fewer than 2^20
+//   contributions.  The resolution 2^-s is about 2^-42 B, far below the FP32
+//   rounding of the contributions themselves, and the tile sum is exact and
+//   independent of the order of the adds.
+constexpr int kRounds = 32;
+constexpr int kOrderChunk = 2048;
+constexpr int kFixedLoBits = 12;
+constexpr int kFixedRange = 42;
+template <typename T>
+struct LaneLayout {
+  static constexpr bool cell_rounds = sizeof(T) == 4;
+  static constexpr bool fixed_j = sizeof(T) == 4;
+};
+
 template <typename T>
 size_t tiled_smem_bytes(const Tiles& tl) {
-  return sizeof(T) * (6 * (size_t)stage_n(tl) + 3 * (size_t)jtile_n(tl));
+  const size_t jword = LaneLayout<T>::fixed_j ? 8 : sizeof(T);
+  size_t b = sizeof(T) * 6 * (size_t)stage_n(tl) + jword * 3 * (size_t)jtile_n(tl);
+  if (LaneLayout<T>::cell_rounds) b += 4 * ((size_t)tl.tx * tl.ty * tl.tz + 3 * kRounds) + 2 * (size_t)kOrderChunk;
+  if (LaneLayout<T>::fixed_j) b += 16;  // the three scale exponents and the weight sum
+  return b;
+}
+
+// The shared-memory J tile of one CTA: [3][nJ] values over the cells
+// [o3, o3 + t + 5) per axis, as T (FP64) or as fixed-point word pairs (FP32).
+template <typename T>
+struct JTile {
+  T* f;
+  unsigned* hi;
+  unsigned* lo;
+  const int* s;  // fixed point: scale exponent per component
+  int nJ, JY, JZ;
+};
+
+// x rounded to the nearest integer, for |x| < 2^22 (the float 1.5 * 2^23
+// puts the integer part in the low mantissa bits).
+__device__ __forceinline__ int round_small(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
+
+__device__ __forceinline__ void red_u32(unsigned* a, unsigned v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(a)), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -47,22 +98,22 @@ __device__ __forceinline__ int warp_count(int* counter, int key, bool want_base,
   return __popc(m & lanemask_lt());
 }
 
-// Gather one field component from the staged tile: 4x4x4 separable sum,
-// contracting z first, then y, then x.
-template <typename T>
+// Gather one field component from the staged tile: NA x NB x NC separable
+// sum (4 nodes along a node-centred axis; 4, or 5 with one zero weight, along
+// a half-staggered one), contracting z first, then y, then x.
+template <int NA, int NB, int NC, typename T>
 __device__ __forceinline__ T gather_smem(const T* __restrict__ s, int SY, int SZ, int bx, int by, int bz,
                                          const T* wx, const T* wy, const T* wz) {
   T ax = T(0);
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
+  for (int a = 0; a < NA; ++a) {
     T ay = T(0);
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < NB; ++b) {
       const T* row = s + ((bx + a) * SY + (by + b)) * SZ + bz;
       T az = row[0] * wz[0];
-      az = fma(row[1], wz[1], az);
-      az = fma(row[2], wz[2], az);
-      az = fma(row[3], wz[3], az);
+#pragma unroll
+      for (int c = 1; c < NC; ++c) az = fma(row[c], wz[c], az);
       ay = fma(az, wy[b], ay);
     }
     ax = fma(ay, wx[a], ax);
@@ -81,9 +132,238 @@ __device__ __forceinline__ bool lt_zero(float o) { return o < 0.0f; }
 __device__ __forceinline__ bool ge_one(float o) { return o >= 1.0f; }
 __device__ __forceinline__ bool lt_half(float o) { return o < 0.5f; }
 
+// Gather, Boris push, move and Esirkepov deposit of particle pi of the tile
+// whose staged origin is o3; returns its destination tile key (-1: absorbed).
+template <typename T>
+__device__ __forceinline__ int push_particle(const Geom<T>& g, const Tiles& tl, const Parts<T>& p, int pi,
+                                             const int o3[3], const T* __restrict__ sF, int nS, int SY, int SZ,
+                                             const JTile<T>& jt, T h, T q, int origin_after, int xlo, int xhi,
+                                             int* __restrict__ keys, int* err) {
+  const int N[3] = {g.nx, g.ny, g.nz};
+  const T dtd[3] = {g.dt / g.dx, g.dt / g.dy, g.dt / g.dz};
+  const T jc[3] = {T(-1) / (g.dt * g.dy * g.dz), T(-1) / (g.dt * g.dx * g.dz), T(-1) / (g.dt * g.dx * g.dy)};
+  const T third = T(1) / T(3);
+  const int cell = p.cell[pi];
+  int c0[3];
+  c0[0] = cell / g.nyz;
+  const int rem = cell - c0[0] * g.nyz;
+  c0[1] = rem / g.nz;
+  c0[2] = rem - c0[1] * g.nz;
+  int lc[3];
+  T o0[3], u[3];
+  const int text[3] = {tl.tx, tl.ty, tl.tz};
+  bool inside = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lc[d] = c0[d] - o3[d];  // in [2, t+2) for a particle of this tile
+    inside = inside && lc[d] >= 2 && lc[d] < text[d] + 2;
+    o0[d] = p.o[d][pi];
+    u[d] = p.u[d][pi];
+  }
+  if (!inside) {  // never expected: keeps every shared-memory index in range
+    atomicOr(err, 4);
+    keys[pi] = -1;
+    return -1;
+  }
+  T wn[3][4];
+  int bn[3];
+  T E[3], B[3];
+  T wh[3][4];
+  int bh[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    bspline3(o0[d], wn[d]);
+    const bool lo = lt_half(o0[d]);
+    bspline3(lo ? o0[d] + T(0.5) : o0[d] - T(0.5), wh[d]);
+    bn[d] = lc[d] - 1;
+    bh[d] = lc[d] - (lo ? 2 : 1);
+  }
+  E[0] = gather_smem<4, 4, 4>(sF + 0 * nS, SY, SZ, bh[0], bn[1], bn[2], wh[0], wn[1], wn[2]);
+  E[1] = gather_smem<4, 4, 4>(sF + 1 * nS, SY, SZ, bn[0], bh[1], bn[2], wn[0], wh[1], wn[2]);
+  E[2] = gather_smem<4, 4, 4>(sF + 2 * nS, SY, SZ, bn[0], bn[1], bh[2], wn[0], wn[1], wh[2]);
+  B[0] = gather_smem<4, 4, 4>(sF + 3 * nS, SY, SZ, bn[0], bh[1], bh[2], wn[0], wh[1], wh[2]);
+  B[1] = gather_smem<4, 4, 4>(sF + 4 * nS, SY, SZ, bh[0], bn[1], bh[2], wh[0], wn[1], wh[2]);
+  B[2] = gather_smem<4, 4, 4>(sF + 5 * nS, SY, SZ, bh[0], bh[1], bn[2], wh[0], wh[1], wn[2]);
+
+  // relativistic Boris push
+  T um[3], tv[3], sv[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) um[d] = u[d] + h * E[d];
+  const T hg = h * rsqrt(T(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);  // h / gamma-
+#pragma unroll
+  for (int d = 0; d < 3; ++d) tv[d] = hg * B[d];
+  const T s2 = T(2) / (T(1) + tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) sv[d] = s2 * tv[d];
+  const T px = um[0] + (um[1] * tv[2] - um[2] * tv[1]);
+  const T py = um[1] + (um[2] * tv[0] - um[0] * tv[2]);
+  const T pz = um[2] + (um[0] * tv[1] - um[1] * tv[0]);
+  u[0] = um[0] + (py * sv[2] - pz * sv[1]) + h * E[0];
+  u[1] = um[1] + (pz * sv[0] - px * sv[2]) + h * E[1];
+  u[2] = um[2] + (px * sv[1] - py * sv[0]) + h * E[2];
+  T ig = rsqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);  // 1 / gamma
+  // a non-finite momentum (a blown-up state) is reported and the particle
+  // absorbed without moving or depositing, so that the fields stay finite
+  const bool bad = !(ig > T(0));
+  if (bad) {
+    atomicOr(err, 8);
+    ig = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u[d] = T(0);
+  }
+
+  // position update (cell + offset), |move| < 1 cell per axis
+  T o1[3];
+  int dc[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T o = o0[d] + dtd[d] * u[d] * ig;
+    int k = 0;
+    if (lt_zero(o)) {
+      o += T(1);
+      k = -1;
+    } else if (ge_one(o)) {
+      o -= T(1);
+      k = 1;
+    }
+    if (ge_one(o)) {
+      o = T(0);
+      k += 1;
+    }
+    o1[d] = o;
+    dc[d] = k;
+  }
+
+  // Esirkepov deposit into the shared J tile: 5-node window per axis
+  // starting at c0 - 1 + min(dc, 0); S0 on window nodes p0..p0+3, S1 on
+  // p1..p1+3.  Wx(i,j,k) = DSx(i) A(j,k) with A = S0y S0z + DSy S0z/2 +
+  // S0y DSz/2 + DSy DSz/3 = S0y (S0z + DSz/2) + DSy (S0z/2 + DSz/3).
+  // A particle that stays in its cell along an axis has a 4-node support
+  // there (node 5 of the window carries nothing): nw = 4 or 5 nodes, and
+  // the running sum along the current's own axis vanishes on its last
+  // node, so only nw - 1 current values are nonzero.
+  T S0[3][5], DS[3][5];
+  int lw[3], nw[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T w1[4];
+    bspline3(o1[d], w1);
+    const int p0 = dc[d] < 0 ? 1 : 0, p1 = dc[d] > 0 ? 1 : 0;
+    lw[d] = lc[d] - 1 - p0;
+    nw[d] = dc[d] != 0 ? 5 : 4;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const T a0 = p0 ? (m > 0 ? wn[d][m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? wn[d][m < 4 ? m : 3] : T(0));
+      const T a1 = p1 ? (m > 0 ? w1[m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? w1[m < 4 ? m : 3] : T(0));
+      S0[d][m] = a0;
+      DS[d][m] = a1 - a0;
+    }
+  }
+  const T qw = bad ? T(0) : q * p.w[pi];
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp) {
+    // axis `comp` carries the running sum; (b, c) are the other two axes
+    const int ab = comp == 0 ? 1 : 0, ac = comp == 2 ? 1 : 2;
+    T P[4];
+    T run = T(0);
+    const T cf = qw * jc[comp];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      run += DS[comp][m];
+      P[m] = cf * run;
+    }
+    T ak[5], bk[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      ak[m] = S0[ac][m] + T(0.5) * DS[ac][m];
+      bk[m] = T(0.5) * S0[ac][m] + third * DS[ac][m];
+    }
+    // strides of the three axes in the J tile; (m, b, c) walk (comp, ab, ac)
+    const int st[3] = {jt.JY * jt.JZ, jt.JZ, 1};
+    const int base0 = comp * jt.nJ + lw[0] * st[0] + lw[1] * st[1] + lw[2] * st[2];
+    const int sm_ = st[comp], sb_ = st[ab], sc_ = st[ac];
+    const int nm = nw[comp] - 1, nb = nw[ab], nc = nw[ac];
+    if constexpr (LaneLayout<T>::fixed_j) {
+      // P[m] with a per-particle exponent kp (|P 2^kp| in [2^21, 2^22)), A
+      // with 2^21; their product carries 2^(kp + 21), shifted to the tile's
+      // 2^s with rounding to nearest
+      const float pmax = fmaxf(fmaxf(fabsf(P[0]), fabsf(P[1])), fmaxf(fabsf(P[2]), fabsf(P[3])));
+      const int ep = ((__float_as_int(pmax) >> 23) & 255) - 127;
+      if (ep > -100) {  // else the particle carries no current along this axis (or below 2^-100)
+        const int kp = 21 - ep;
+        const float sp = __int_as_float((127 + kp) << 23);
+        int Pi[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) Pi[m] = round_small(P[m] * sp);
+        const int sh = min(max(kp + 21 - jt.s[comp], 0), 62);
+        const long long half = (1LL << sh) >> 1;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          if (b < nb) {
+            const T sb = S0[ab][b], db = DS[ab][b];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+              if (c < nc) {
+                const int Ai = round_small((sb * ak[c] + db * bk[c]) * 2097152.0f);
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                  if (m < nm) {
+                    const long long X = ((long long)Pi[m] * Ai + half) >> sh;
+                    const int idx = base0 + m * sm_ + b * sb_ + c * sc_;
+                    red_u32(jt.hi + idx, (unsigned)(X >> kFixedLoBits));
+                    red_u32(jt.lo + idx, (unsigned)X & ((1u << kFixedLoBits) - 1u));
+                  }
+              }
+            }
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        if (b < nb) {
+          const T sb = S0[ab][b], db = DS[ab][b];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            if (c < nc) {
+              const T A = sb * ak[c] + db * bk[c];
+#pragma unroll
+              for (int m = 0; m < 4; ++m)
+                if (m < nm) atomicAdd(jt.f + base0 + m * sm_ + b * sb_ + c * sc_, P[m] * A);
+            }
+          }
+        }
+      }
+    }
+  }
+
+  // store in place; the key is the destination tile (or -1: absorbed)
+  const int n0 = wrapi(c0[0] + dc[0], N[0]);
+  const int n1 = wrapi(c0[1] + dc[1], N[1]);
+  const int n2 = wrapi(c0[2] + dc[2], N[2]);
+  p.cell[pi] = n0 * g.nyz + n1 * g.nz + n2;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    p.o[d][pi] = o1[d];
+    p.u[d][pi] = u[d];
+  }
+  int key = tile_of(g, tl, n0, n1, n2);
+  if (!g.periodic_x) {
+    int rel = n0 - origin_after;
+    if (rel < 0) rel += g.nx;
+    if (rel < xlo || rel > xhi) key = -1;
+  }
+  // absorbing layers: a particle that leaves the y, z cells [L, n - L) is absorbed
+  if (g.pml && (n1 < g.pml || n1 >= g.ny - g.pml || n2 < g.pml || n2 >= g.nz - g.pml)) key = -1;
+  if (bad) key = -1;
+  keys[pi] = key;
+  return key;
+}
+
 // One CTA per tile.  keys[p] receives the particle's tile after the move (or
 // -1 when it leaves the open-x range once the window has moved to
 // origin_after); cnt_next[tile] counts the particles each tile will hold.
+// blockDim.x is 256.
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom<T> g, Tiles tl, Fields<T> f, Parts<T> p,
                                                    const int* __restrict__ tstart, int capacity,
@@ -100,10 +380,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom
   const int tyi = rest % tl.nty, txi = rest / tl.nty;
   const int o3[3] = {txi * tl.tx - 2, tyi * tl.ty - 2, tzi * tl.tz - 2};  // staged origin (cells)
   const int SX = tl.tx + 4, SY = tl.ty + 4, SZ = tl.tz + 4;
-  const int JY = tl.ty + 5, JZ = tl.tz + 5;
   const int nS = SX * SY * SZ, nJ = jtile_n(tl);
   T* sF = sm;
-  T* sJ = sm + 6 * nS;
+  JTile<T> jt;
+  jt.nJ = nJ;
+  jt.JY = tl.ty + 5;
+  jt.JZ = tl.tz + 5;
+  unsigned char* after_j;
+  int* sexp = nullptr;
+  if constexpr (LaneLayout<T>::fixed_j) {
+    jt.f = nullptr;
+    jt.hi = reinterpret_cast<unsigned*>(sm + 6 * nS);
+    jt.lo = jt.hi + 3 * nJ;
+    sexp = reinterpret_cast<int*>(jt.lo + 3 * nJ);
+    jt.s = sexp;
+    after_j = reinterpret_cast<unsigned char*>(sexp + 4);
+  } else {
+    jt.f = sm + 6 * nS;
+    jt.hi = jt.lo = nullptr;
+    jt.s = nullptr;
+    after_j = reinterpret_cast<unsigned char*>(jt.f + 3 * nJ);
+  }
 
   // stage E and B (wrapped storage indices; see the ring note in pic_device.cuh)
   for (int i = threadIdx.x; i < nS; i += blockDim.x) {
@@ -114,231 +411,122 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom
 #pragma unroll
     for (int c = 0; c < 6; ++c) sF[c * nS + i] = f.c[c][gi];
   }
-  for (int i = threadIdx.x; i < 3 * nJ; i += blockDim.x) sJ[i] = T(0);
+  if constexpr (LaneLayout<T>::fixed_j) {
+    for (int i = threadIdx.x; i < 6 * nJ; i += blockDim.x) jt.hi[i] = 0u;
+    // the scale of the fixed-point tile: B = |q jc| sum_p w_p bounds every node
+    float ws = 0.0f;
+    for (int k = threadIdx.x; k < pend - pbeg; k += blockDim.x) ws += fabsf((float)p.w[pbeg + k]);
+    for (int o = 16; o > 0; o >>= 1) ws += __shfl_down_sync(0xffffffffu, ws, o);
+    if (threadIdx.x == 0) sexp[3] = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicAdd(reinterpret_cast<float*>(sexp + 3), ws);
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      const T jcc = threadIdx.x == 0 ? g.dt * g.dy * g.dz : (threadIdx.x == 1 ? g.dt * g.dx * g.dz : g.dt * g.dx * g.dy);
+      // 1.001: margin over the float rounding of the sum
+      const float B = 1.001f * fabsf((float)q) * __int_as_float(sexp[3]) / (float)jcc;
+      const int eb = ((__float_as_int(B) >> 23) & 255) - 127;  // B in [2^eb, 2^(eb+1))
+      sexp[threadIdx.x] = B > 0.0f ? kFixedRange - 1 - eb : 0;
+    }
+  } else {
+    for (int i = threadIdx.x; i < 3 * nJ; i += blockDim.x) jt.f[i] = T(0);
+  }
   if (threadIdx.x == 0) atomicAdd(pushed, (unsigned long long)(pend - pbeg));
   __syncthreads();
-
-  const int N[3] = {g.nx, g.ny, g.nz};
-  const T dtd[3] = {g.dt / g.dx, g.dt / g.dy, g.dt / g.dz};
-  const T jc[3] = {T(-1) / (g.dt * g.dy * g.dz), T(-1) / (g.dt * g.dx * g.dz), T(-1) / (g.dt * g.dx * g.dy)};
-  const T third = T(1) / T(3);
-
-  // Lane order.  Particles that share a cell sit next to each other in a
-  // tile's list (loading and the stable scatter keep their order), so with
-  // consecutive lanes the deposit atomics of a warp often hit an address
-  // twice.  FP32: each chunk of 64 particles goes to a pair of warps, the
-  // even ones to the first and the odd ones to the second, so that list
-  // neighbours never share a warp while a warp's lanes still cover a run of
-  // neighbouring cells, as the gather's shared-memory reads prefer.  FP64:
-  // the lanes of a warp take particles mrow apart in the list, which also
-  // spreads the many particles of a dense cell (bubble walls) over warps.
-  // Measured on a run's state, each better than the other order for its
-  // precision.  blockDim.x is 256 (four warp pairs).
-  constexpr bool kSpread = sizeof(T) == 8;
   const int ntile = pend - pbeg;
-  const int mrow = (ntile + 31) >> 5;
-  const int nloop = kSpread ? 32 * mrow : ntile;
-  for (int base = 0; base < nloop; base += blockDim.x) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int pi;  // pi >= pend: no particle
-    if (kSpread) {
+
+  if constexpr (LaneLayout<T>::cell_rounds) {
+    // cell-round order, chunk by chunk of the tile's list
+    const int ncell_t = tl.tx * tl.ty * tl.tz;
+    int* hist = reinterpret_cast<int*>(after_j);
+    int* rtot = hist + ncell_t;
+    int* rbase = rtot + kRounds;
+    int* rfill = rbase + kRounds;
+    unsigned short* order = reinterpret_cast<unsigned short*>(rfill + kRounds);
+    constexpr int kPer = kOrderChunk / 256;
+    for (int ch0 = 0; ch0 < ntile; ch0 += kOrderChunk) {
+      const int nch = min(kOrderChunk, ntile - ch0);
+      for (int i = threadIdx.x; i < ncell_t; i += blockDim.x) hist[i] = 0;
+      if (threadIdx.x < 3 * kRounds) rtot[threadIdx.x] = 0;
+      __syncthreads();
+      int rk[kPer];
+#pragma unroll
+      for (int it = 0; it < kPer; ++it) {
+        const int k = it * 256 + threadIdx.x;
+        int r = -1;
+        if (k < nch) {
+          const int cell = p.cell[pbeg + ch0 + k];
+          const int cx = cell / g.nyz, rem = cell - cx * g.nyz;
+          const int cy = rem / g.nz, cz = rem - cy * g.nz;
+          const int lx = cx - o3[0] - 2, ly = cy - o3[1] - 2, lz = cz - o3[2] - 2;
+          const bool in = lx >= 0 && lx < tl.tx && ly >= 0 && ly < tl.ty && lz >= 0 && lz < tl.tz;
+          const int lcell = in ? (lx * tl.ty + ly) * tl.tz + lz : 0;  // a stray particle (caught later) ranks in cell 0
+          r = min(atomicAdd(hist + lcell, 1), kRounds - 1);
+        }
+        rk[it] = r;
+        warp_count(rtot, r, false, nullptr);
+      }
+      __syncthreads();
+      if (threadIdx.x < 32) {  // exclusive scan of the round sizes (kRounds = 32)
+        const int v = rtot[threadIdx.x];
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int n = __shfl_up_sync(0xffffffffu, incl, o);
+          if (threadIdx.x >= o) incl += n;
+        }
+        rbase[threadIdx.x] = incl - v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int it = 0; it < kPer; ++it) {
+        int off;
+        const int rank = warp_count(rfill, rk[it], true, &off);
+        if (rk[it] >= 0) order[rbase[rk[it]] + off + rank] = (unsigned short)(it * 256 + threadIdx.x);
+      }
+      __syncthreads();
+      for (int base = 0; base < nch; base += blockDim.x) {
+        const int k = base + threadIdx.x;
+        int key = -2;
+        if (k < nch)
+          key = push_particle(g, tl, p, pbeg + ch0 + order[k], o3, sF, nS, SY, SZ, jt, h, q, origin_after,
+                              xlo, xhi, keys, err);
+        warp_count(cnt_next, key, false, nullptr);
+      }
+      __syncthreads();  // the next chunk reuses the histogram and the order
+    }
+  } else {
+    // FP64: the lanes of a warp take particles mrow apart in the list, which
+    // spreads the many particles of a dense cell (bubble walls) over warps.
+    const int mrow = (ntile + 31) >> 5;
+    const int nloop = 32 * mrow;
+    for (int base = 0; base < nloop; base += blockDim.x) {
+      const int lane = threadIdx.x & 31;
       const int kk = base + threadIdx.x;
       const int loc = lane * mrow + (kk >> 5);
-      pi = (kk < nloop && loc < ntile) ? pbeg + loc : pend;
-    } else {
-      pi = pbeg + base + ((w >> 1) << 6) + (lane << 1) + (w & 1);
+      int key = -2;
+      if (kk < nloop && loc < ntile)
+        key = push_particle(g, tl, p, pbeg + loc, o3, sF, nS, SY, SZ, jt, h, q, origin_after, xlo, xhi, keys,
+                            err);
+      warp_count(cnt_next, key, false, nullptr);
     }
-    int key = -2;
-    if (pi < pend) {
-      const int cell = p.cell[pi];
-      int c0[3];
-      c0[0] = cell / g.nyz;
-      const int rem = cell - c0[0] * g.nyz;
-      c0[1] = rem / g.nz;
-      c0[2] = rem - c0[1] * g.nz;
-      int lc[3];
-      T o0[3], u[3];
-      const int text[3] = {tl.tx, tl.ty, tl.tz};
-      bool inside = true;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        lc[d] = c0[d] - o3[d];  // in [2, t+2) for a particle of this tile
-        inside = inside && lc[d] >= 2 && lc[d] < text[d] + 2;
-        o0[d] = p.o[d][pi];
-        u[d] = p.u[d][pi];
-      }
-      if (!inside) {  // never expected: keeps every shared-memory index in range
-        atomicOr(err, 4);
-        keys[pi] = -1;
-        key = -1;
-      } else {
-      T wn[3][4], wh[3][4];
-      int bn[3], bh[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        bspline3(o0[d], wn[d]);
-        const bool lo = lt_half(o0[d]);
-        bspline3(lo ? o0[d] + T(0.5) : o0[d] - T(0.5), wh[d]);
-        bn[d] = lc[d] - 1;
-        bh[d] = lc[d] - (lo ? 2 : 1);
-      }
-      T E[3], B[3];
-      E[0] = gather_smem(sF + 0 * nS, SY, SZ, bh[0], bn[1], bn[2], wh[0], wn[1], wn[2]);
-      E[1] = gather_smem(sF + 1 * nS, SY, SZ, bn[0], bh[1], bn[2], wn[0], wh[1], wn[2]);
-      E[2] = gather_smem(sF + 2 * nS, SY, SZ, bn[0], bn[1], bh[2], wn[0], wn[1], wh[2]);
-      B[0] = gather_smem(sF + 3 * nS, SY, SZ, bn[0], bh[1], bh[2], wn[0], wh[1], wh[2]);
-      B[1] = gather_smem(sF + 4 * nS, SY, SZ, bh[0], bn[1], bh[2], wh[0], wn[1], wh[2]);
-      B[2] = gather_smem(sF + 5 * nS, SY, SZ, bh[0], bh[1], bn[2], wh[0], wh[1], wn[2]);
-
-      // relativistic Boris push
-      T um[3], tv[3], sv[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) um[d] = u[d] + h * E[d];
-      const T hg = h * rsqrt(T(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);  // h / gamma-
-#pragma unroll
-      for (int d = 0; d < 3; ++d) tv[d] = hg * B[d];
-      const T s2 = T(2) / (T(1) + tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2]);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) sv[d] = s2 * tv[d];
-      const T px = um[0] + (um[1] * tv[2] - um[2] * tv[1]);
-      const T py = um[1] + (um[2] * tv[0] - um[0] * tv[2]);
-      const T pz = um[2] + (um[0] * tv[1] - um[1] * tv[0]);
-      u[0] = um[0] + (py * sv[2] - pz * sv[1]) + h * E[0];
-      u[1] = um[1] + (pz * sv[0] - px * sv[2]) + h * E[1];
-      u[2] = um[2] + (px * sv[1] - py * sv[0]) + h * E[2];
-      T ig = rsqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);  // 1 / gamma
-      // a non-finite momentum (a blown-up state) is reported and the particle
-      // absorbed without moving or depositing, so that the fields stay finite
-      const bool bad = !(ig > T(0));
-      if (bad) {
-        atomicOr(err, 8);
-        ig = T(0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) u[d] = T(0);
-      }
-
-      // position update (cell + offset), |move| < 1 cell per axis
-      T o1[3];
-      int dc[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        T o = o0[d] + dtd[d] * u[d] * ig;
-        int k = 0;
-        if (lt_zero(o)) {
-          o += T(1);
-          k = -1;
-        } else if (ge_one(o)) {
-          o -= T(1);
-          k = 1;
-        }
-        if (ge_one(o)) {
-          o = T(0);
-          k += 1;
-        }
-        o1[d] = o;
-        dc[d] = k;
-      }
-
-      // Esirkepov deposit into the shared J tile: 5-node window per axis
-      // starting at c0 - 1 + min(dc, 0); S0 on window nodes p0..p0+3, S1 on
-      // p1..p1+3.  Wx(i,j,k) = DSx(i) A(j,k) with A = S0y S0z + DSy S0z/2 +
-      // S0y DSz/2 + DSy DSz/3 = S0y (S0z + DSz/2) + DSy (S0z/2 + DSz/3).
-      // A particle that stays in its cell along an axis has a 4-node support
-      // there (node 5 of the window carries nothing): nw = 4 or 5 nodes, and
-      // the running sum along the current's own axis vanishes on its last
-      // node, so only nw - 1 current values are nonzero.
-      T S0[3][5], DS[3][5];
-      int lw[3], nw[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        T w1[4];
-        bspline3(o1[d], w1);
-        const int p0 = dc[d] < 0 ? 1 : 0, p1 = dc[d] > 0 ? 1 : 0;
-        lw[d] = lc[d] - 1 - p0;
-        nw[d] = dc[d] != 0 ? 5 : 4;
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-          const T a0 = p0 ? (m > 0 ? wn[d][m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? wn[d][m < 4 ? m : 3] : T(0));
-          const T a1 = p1 ? (m > 0 ? w1[m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? w1[m < 4 ? m : 3] : T(0));
-          S0[d][m] = a0;
-          DS[d][m] = a1 - a0;
-        }
-      }
-      const T qw = bad ? T(0) : q * p.w[pi];
-#pragma unroll
-      for (int comp = 0; comp < 3; ++comp) {
-        // axis `comp` carries the running sum; (b, c) are the other two axes
-        const int ab = comp == 0 ? 1 : 0, ac = comp == 2 ? 1 : 2;
-        T P[4];
-        T run = T(0);
-        const T cf = qw * jc[comp];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          run += DS[comp][m];
-          P[m] = cf * run;
-        }
-        T ak[5], bk[5];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-          ak[m] = S0[ac][m] + T(0.5) * DS[ac][m];
-          bk[m] = T(0.5) * S0[ac][m] + third * DS[ac][m];
-        }
-        T* J = sJ + comp * nJ;
-        // strides of the three axes in the J tile; (m, b, c) walk (comp, ab, ac)
-        const int st[3] = {JY * JZ, JZ, 1};
-        const int base0 = lw[0] * st[0] + lw[1] * st[1] + lw[2] * st[2];
-        const int sm_ = st[comp], sb_ = st[ab], sc_ = st[ac];
-        const int nm = nw[comp] - 1, nb = nw[ab], nc = nw[ac];
-#pragma unroll
-        for (int b = 0; b < 5; ++b) {
-          if (b < nb) {
-            const T sb = S0[ab][b], db = DS[ab][b];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-              if (c < nc) {
-                const T A = sb * ak[c] + db * bk[c];
-#pragma unroll
-                for (int m = 0; m < 4; ++m)
-                  if (m < nm) atomicAdd(J + base0 + m * sm_ + b * sb_ + c * sc_, P[m] * A);
-              }
-            }
-          }
-        }
-      }
-
-      // store in place; the key is the destination tile (or -1: absorbed)
-      const int n0 = wrapi(c0[0] + dc[0], N[0]);
-      const int n1 = wrapi(c0[1] + dc[1], N[1]);
-      const int n2 = wrapi(c0[2] + dc[2], N[2]);
-      p.cell[pi] = n0 * g.nyz + n1 * g.nz + n2;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        p.o[d][pi] = o1[d];
-        p.u[d][pi] = u[d];
-      }
-      key = tile_of(g, tl, n0, n1, n2);
-      if (!g.periodic_x) {
-        int rel = n0 - origin_after;
-        if (rel < 0) rel += g.nx;
-        if (rel < xlo || rel > xhi) key = -1;
-      }
-      // absorbing layers: a particle that leaves the y, z cells [L, n - L) is absorbed
-      if (g.pml && (n1 < g.pml || n1 >= g.ny - g.pml || n2 < g.pml || n2 >= g.nz - g.pml)) key = -1;
-      if (bad) key = -1;
-      keys[pi] = key;
-      }
-    }
-    warp_count(cnt_next, key, false, nullptr);
+    __syncthreads();
   }
-  __syncthreads();
 
   // flush the J tile (cells [o3, o3 + t + 5) per axis, wrapped)
   for (int i = threadIdx.x; i < 3 * nJ; i += blockDim.x) {
-    const T v = sJ[i];
-    if (v == T(0)) continue;
     const int comp = i / nJ, li = i - comp * nJ;
-    const int lz = li % JZ, r = li / JZ;
-    const int ly = r % JY, lx = r / JY;
+    T v;
+    if constexpr (LaneLayout<T>::fixed_j) {
+      const long long X = (long long)(int)jt.hi[i] * (1LL << kFixedLoBits) + (long long)jt.lo[i];
+      if (X == 0) continue;
+      v = ldexpf((float)X, -sexp[comp]);
+    } else {
+      v = jt.f[i];
+      if (v == T(0)) continue;
+    }
+    const int lz = li % jt.JZ, r = li / jt.JZ;
+    const int ly = r % jt.JY, lx = r / jt.JY;
     const size_t gi = (size_t)wrapi(o3[0] + lx, g.nx) * g.nyz + (size_t)wrapi(o3[1] + ly, g.ny) * g.nz +
                       wrapi(o3[2] + lz, g.nz);
     atomicAdd(f.c[JX + comp] + gi, v);

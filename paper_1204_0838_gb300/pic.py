@@ -23,6 +23,7 @@ PIC_LOAD_RANDOM, PIC_LOAD_LATTICE = 0, 1
 PIC_LASER_AUTO, PIC_LASER_HARD_SOURCE, PIC_LASER_IN_BOX = 0, 1, 2
 PIC_DIAG_EX_LINEOUT, PIC_DIAG_FIELD_ENERGY, PIC_DIAG_CHARGE, PIC_DIAG_SPECTRUM = 0, 1, 2, 3
 PIC_DIAG_EMITTANCE, PIC_DIAG_PHASE_X_PX, PIC_DIAG_DENSITY_XY = 4, 5, 6
+PIC_DIAG_DIVE_RESIDUAL = 7
 PIC_FLAG_TRACK_IDS = 1
 COMPONENTS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz"]
 
@@ -435,8 +436,10 @@ class Sim:
         kinds = {"ex_lineout": PIC_DIAG_EX_LINEOUT, "field_energy": PIC_DIAG_FIELD_ENERGY,
                  "charge": PIC_DIAG_CHARGE, "spectrum": PIC_DIAG_SPECTRUM,
                  "emittance": PIC_DIAG_EMITTANCE, "phase_x_px": PIC_DIAG_PHASE_X_PX,
-                 "density_xy": PIC_DIAG_DENSITY_XY}
+                 "density_xy": PIC_DIAG_DENSITY_XY, "dive_residual": PIC_DIAG_DIVE_RESIDUAL}
         k = kinds[kind]
+        if k == PIC_DIAG_DIVE_RESIDUAL:
+            return pic_diag(self.h, k, max(length, 1))
         if k == PIC_DIAG_EMITTANCE:
             return pic_diag(self.h, k, 2, gamma_min=p0)
         if k == PIC_DIAG_PHASE_X_PX:

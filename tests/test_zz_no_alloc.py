@@ -6,8 +6,10 @@ cudaMalloc/cudaFree would synchronise the device, code running inside another
 library's callbacks).  pic_diag_noalloc runs the same reductions as pic_diag
 with its scratch in a fixed device array.  This test calls it through the
 C-ABI and checks that two calls in a row give what pic_diag gives, for every
-diagnostic kind, on both precisions, and that an over-long request is
-refused.  The file name makes pytest collect it last.
+diagnostic kind, on both precisions, that the calls allocate nothing (the
+handle's device memory comes from counting hooks, and pic_diag, called after,
+is seen to allocate through them), and that an over-long request is refused.
+The file name makes pytest collect it last.
 """
 import numpy as np
 import pytest
@@ -27,14 +29,26 @@ def _cuda():
     pic.lib()
 
 
-def _sim(precision):
+class CountingMemory(pic.TorchMemory):
+    """The torch-backed pic_alloc hooks, counting the allocations made."""
+
+    def __init__(self):
+        self.allocs = 0
+        super().__init__()
+
+    def _alloc(self, nbytes, ctx):
+        self.allocs += 1
+        return super()._alloc(nbytes, ctx)
+
+
+def _sim(precision, memory=None):
     cfg = W.config("c1", crop=(96, 24, 24))
     cfg["x0"] = -48 * cfg["dx"]
     cfg["fwhm"], cfg["waist"], cfg["t_peak"] = 4e-15, 3e-6, 40 * cfg["dx"] / W.C0
     cfg["prof_x"], cfg["prof_n"] = [0.0, 2e-6, 1.0], [0.0, 0.02, 0.02]
     g = pic.Sim(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"], cfg["lambda0"],
                 x0=cfg["x0"], periodic_x=False, precision=precision, seed=cfg["seed"],
-                window=cfg["window"])
+                window=cfg["window"], memory=memory)
     g.add_species(cfg["prof_x"], cfg["prof_n"], cfg["ppc"], loading=cfg["loading"])
     g.add_laser(cfg["a0"], cfg["waist"], cfg["fwhm"], cfg["lambda0"], cfg["x_focus"], cfg["t_peak"])
     g.step(40)
@@ -47,17 +61,36 @@ def _close(a, b):
     return np.abs(a - b).max() <= TOL * scale
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_noalloc_diag_matches_pic_diag_on_two_calls(precision):
-    g, cfg = _sim(precision)
-    nx = cfg["nx"]
-    requests = [
+def _requests(nx):
+    return [
         (pic.PIC_DIAG_EX_LINEOUT, nx, {}),
         (pic.PIC_DIAG_FIELD_ENERGY, 1, {}),
         (pic.PIC_DIAG_CHARGE, 1, {"gamma_min": 1.0001}),
         (pic.PIC_DIAG_CHARGE, 1, {"gamma_min": 0.0}),
         (pic.PIC_DIAG_SPECTRUM, 64, {"e_min": 0.0, "e_max": 0.2}),
     ]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_noalloc_diag_allocates_nothing(precision):
+    mem = CountingMemory()
+    g, cfg = _sim(precision, memory=mem)
+    before = mem.allocs
+    assert before > 0  # the handle's own memory came through the hooks
+    results = [pic.pic_diag_noalloc(g.h, kind, length, **kw) for kind, length, kw in _requests(cfg["nx"])]
+    assert mem.allocs == before
+    # the check is sensitive: pic_diag's first request allocates its scratch through the hooks
+    ref = [pic.pic_diag(g.h, kind, length, **kw) for kind, length, kw in _requests(cfg["nx"])]
+    assert mem.allocs > before
+    for a, b in zip(results, ref):
+        assert _close(a, b)
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_noalloc_diag_matches_pic_diag_on_two_calls(precision):
+    g, cfg = _sim(precision)
+    requests = _requests(cfg["nx"])
     for kind, length, kw in requests:
         ref = pic.pic_diag(g.h, kind, length, **kw)
         first = pic.pic_diag_noalloc(g.h, kind, length, **kw)
