@@ -36,12 +36,20 @@ UNIT = "particle-steps/s"
 # 4-node support per axis (a particle that crosses a cell face needs more):
 # weights 138, gather 882, Boris 54, position 17, deposit 522 (FMA = 2 flop).
 FLOP_PER_PARTICLE = 1613
-BYTES_PER_PARTICLE = {"fp64": 112, "fp32": 60}  # SoA record read once, written once
+# Algorithmic DRAM bytes of k_push_tiled per particle: the SoA record read
+# and written once (FP64 112 B, FP32 60 B), plus per cell the E, B read by the
+# gather and the J written (FP64 72 B, FP32 36 B) shared by the ppc particles
+# of the cell.
+ALG_BYTES_PER_PARTICLE = {"fp64": lambda ppc: 112 + 72 / ppc, "fp32": lambda ppc: 60 + 36 / ppc}
 # DRAM bytes (read + write) per particle of k_push_tiled, from one ncu capture
 # of the current kernel on a 256x128x128 window in a run's own state (run for
-# 256 steps past a load at rest), FP64 8x8x16 and FP32 8x8x8 tiles; traffic
-# per launch scales with the particles processed.
-NCU_TRAFFIC_PER_PARTICLE = {"fp64": 1325.259776e6 / 8336282, "fp32": 699.216640e6 / 8336282}
+# 256 steps past a load at rest), 8x8x8 tiles; traffic per launch scales with
+# the particles processed.
+NCU_TRAFFIC_PER_PARTICLE = {"fp64": (808.351488e6 + 518.660096e6) / 8336282, "fp32": (420.643328e6 + 273.170688e6) / 8336282}
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per particle (c1 spacings, 256x128x128 "
+                  "window in a run's state) x particles per launch")
+LIMITER = {"fp64": "FP64 pipe (ncu: ~84 % busy; DRAM < 1 %)",
+           "fp32": "shared-memory pipe (ncu: L1tex ~80 %; DRAM ~3 %)"}
 
 
 def _args():
@@ -51,6 +59,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--legs", default="c2,c3",
+                    help="with --config c1: further legs of the metric timed after it ('' for none)")
     ap.add_argument("--instances", type=int, default=32, help="c3: batched instances")
     ap.add_argument("--start-step", type=int, default=-1)
     ap.add_argument("--crop", default="", help="nx,ny,nz (profiling small cases)")
@@ -94,15 +104,15 @@ def _prerun_steps(start, nx, cold_start):
     return 0 if cold_start else min(start, nx)
 
 
-def _workload(args):
+def _workload(args, name):
     from paper_1204_0838_gb300 import workloads as W
-    start = args.start_step
+    start = args.start_step if name == args.config else -1
     if start < 0:
-        start = {"c0": 0, "c1": 900, "c2": 900, "c3": 450, "c4": 4500}[args.config]
+        start = {"c0": 0, "c1": 900, "c2": 900, "c3": 450, "c4": 4500}[name]
     crop = tuple(int(v) for v in args.crop.split(",")) if args.crop else None
-    nx = W.config(args.config, crop=crop)["nx"]
+    nx = W.config(name, crop=crop)["nx"]
     pre = _prerun_steps(start, nx, args.cold_start)
-    cfg = W.config(args.config, crop=crop, start_step=start - pre)
+    cfg = W.config(name, crop=crop, start_step=start - pre)
     return cfg, start, pre
 
 
@@ -197,7 +207,7 @@ def _fp_peak_tflops(precision, sm_mhz):
 def _oracle_sample():
     """The FP64 CPU oracle on a bounded sample of the c1 workload: the c1
     spacings, loading and laser on a 64x48x48 window that the plasma fills
-    (about 2.9e5 particles), single-threaded."""
+    (about 2.7e5 particles), single-threaded."""
     from oracle import oracle as O
     from paper_1204_0838_gb300 import workloads as W
     cfg = W.config("c1", crop=(64, 48, 48), start_step=2000)
@@ -205,9 +215,15 @@ def _oracle_sample():
               x0=cfg["x0"], periodic_x=False, seed=cfg["seed"], window=cfg["window"])
     o.add_species(cfg["prof_x"], cfg["prof_n"], cfg["ppc"], loading=cfg["loading"])
     o.add_laser(cfg["a0"], cfg["waist"], cfg["fwhm"], cfg["lambda0"], cfg["x_focus"], cfg["t_peak"])
-    desc = ("FP64 C oracle, 1 thread, c1 spacings/loading/laser on a 64x48x48 window filled with "
+    desc = ("FP64 C oracle on the c1 spacings/loading/laser in a 64x48x48 window filled with "
             "plasma (%d particles)" % o.info()["np"])
     return o, desc
+
+
+ORACLE_SAMPLE_CONFIG = {"workload": "sample of c1: 64x48x48 cells, dx=lambda0/24, dy=dz=lambda0/3, 2 ppc "
+                                    "lattice, moving window at c, a0=4, fp64, plasma-filled window "
+                                    "(the c1 window 2000 steps into the run, loaded at rest)",
+                        "grid": [64, 48, 48], "ppc": 2, "precision": "fp64"}
 
 
 def _time_oracle(o, steps):
@@ -219,53 +235,107 @@ def _time_oracle(o, steps):
     return pushed, time.perf_counter() - t0
 
 
-def _oracle_sample_rate(seconds_target=12.0):
-    o, desc = _oracle_sample()
-    o.step(1)
-    pushed, dt = _time_oracle(o, 2)
-    steps = 2
-    while dt < seconds_target:
-        p, d = _time_oracle(o, 2)
+def _oracle_worker(job):
+    """One oracle instance: `warmup` untimed steps, then steps until both
+    `steps` steps and `seconds` seconds are done; returns (particle-steps, s)."""
+    steps, warmup, seconds = job
+    from oracle import build as ob
+    ob.build()
+    o, _ = _oracle_sample()
+    _time_oracle(o, warmup)
+    pushed, dt = _time_oracle(o, steps)
+    while dt < seconds:
+        p, d = _time_oracle(o, 1)
         pushed += p
         dt += d
-        steps += 2
-    return pushed / dt, desc + ", %d steps" % steps, steps
+    return pushed, dt
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(steps, warmup, seconds, cores):
+    """Particle-steps/s of `cores` independent oracle instances run at once
+    (a spawned process pool: the parent may hold a CUDA context), counted as
+    their summed particle-steps over the slowest instance's timed region."""
+    if cores <= 1:
+        pushed, dt = _oracle_worker((steps, warmup, seconds))
+        return pushed / dt, 1, dt
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(steps, warmup, seconds)] * cores)
+    slowest = max(r[1] for r in res)
+    return sum(r[0] for r in res) / slowest, cores, slowest
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle as it stands on the host cores: one instance, and one
+    instance per core at once."""
+    from oracle import build as ob
+    ob.build()
+    _, desc = _oracle_sample()
+    r1, _, _ = oracle_rate(2, 1, seconds, 1)
+    rn, n, _ = oracle_rate(2, 1, seconds, _host_cores())
+    return {"value": rn, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": desc + "; %d independent single-threaded instances at once, each about %.0f s of "
+                             "steps" % (n, seconds),
+            "single_thread": {"value": r1, "cores": 1}}
 
 
 def run_reference(args):
-    """The CPU oracle as it stands, on the host cores (rank 0 only)."""
+    """The CPU oracle as it stands, on the host cores (rank 0 only): one
+    single-threaded instance of the 64x48x48 sample of c1 per core, all at once."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     from oracle import build as ob
     ob.build()
-    cfg, start, pre = _workload(args)
-    o, desc = _oracle_sample()
-    _time_oracle(o, args.warmup)
-    pushed, dt = _time_oracle(o, args.steps)
-    value = pushed / dt
+    _, desc = _oracle_sample()
+    value, cores, slowest = oracle_rate(args.steps, args.warmup, 0.0, _host_cores())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
+            "warmup": args.warmup, "ms_per_step": slowest * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference", "config": _describe(cfg, start, "fp64", pre),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": desc + "; each timed step is one step of this sample"},
+            "data": "synthetic", "impl": "reference", "config": dict(ORACLE_SAMPLE_CONFIG),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc + "; %d independent single-threaded instances at once, each "
+                                              "%d timed steps after %d warm-up steps" % (
+                                                  cores, args.steps, args.warmup)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
-    import torch
-    from paper_1204_0838_gb300 import build as pb
-    from paper_1204_0838_gb300 import pic
+def _roofline(precision, pushes_per_launch, avg_launch_s, ppc, peaks, src, group_ms, steps):
+    """Roofline record of the dominant kernel, k_push_tiled."""
+    achieved = FLOP_PER_PARTICLE * pushes_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else 0.0
+    peak = _fp_peak_tflops(precision, peaks.get("sm_max_mhz", 2070.0))
+    alg = ALG_BYTES_PER_PARTICLE[precision](ppc)
+    hbm = alg * pushes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else None
+    per = NCU_TRAFFIC_PER_PARTICLE.get(precision)
+    return {"kernel": "k_push_tiled (gather + Boris + Esirkepov deposit)",
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None,
+            "traffic": per * pushes_per_launch if per else None,
+            "traffic_source": TRAFFIC_SOURCE if per else "no capture of the current kernel",
+            "peak_source": "derived: 152 SMs x %s FMA lanes x 2 flop x %.0f MHz max clock" % (
+                "128 FP32" if precision == "fp32" else "2 FP64", peaks.get("sm_max_mhz", 2070.0)),
+            "limiter": LIMITER[precision],
+            "hbm_algorithmic_bytes_per_particle": alg,
+            "hbm_achieved_gbs": hbm, "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": src,
+            "hbm_frac": hbm / peaks["hbm_gbs"] if hbm and peaks.get("hbm_gbs") else None,
+            "group_ms_per_step": {k: v / steps for k, v in group_ms.items()}}
 
-    ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
-    torch.cuda.set_device(local)
-    pb.build()
-    cfg, start, pre = _workload(args)
+
+def single_leg(args, name, rank, local, ws):
+    """One instance of config `name` in the run's own state at its start
+    step: K timed steps (CUDA events on the library's stream), then K steps
+    end to end through the C-ABI."""
+    import torch
+    from paper_1204_0838_gb300 import pic
+    cfg, start, pre = _workload(args, name)
     precision = cfg["precision"]
     g = pic.Sim(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"], cfg["lambda0"],
                 x0=cfg["x0"], periodic_x=cfg["periodic_x"], precision=precision, seed=cfg["seed"] + rank,
@@ -287,32 +357,26 @@ def run_ours(args):
         g.step(1)
     torch.cuda.synchronize()
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     stream = torch.cuda.current_stream()
     pushed0 = g.info()["pushed"]
     pic.pic_timing_start(g.h, True)
     clocks = Clocks(local)
     clocks.start()
-    barrier()
+    _barrier(ws)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     pic.pic_step(g.h, args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
-    barrier()
+    _barrier(ws)
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     timing = pic.pic_timing_read(g.h)
     pic.pic_timing_start(g.h, False)
     info = g.info()
-    pushed = info["pushed"] - pushed0
-    # max time / summed particle-steps over ranks
-    ms, pushed = reduce_over_ranks(ms, pushed, ws)
+    pushed_local = info["pushed"] - pushed0
+    ms, pushed = reduce_over_ranks(ms, pushed_local, ws)
     value = pushed / (ms / 1e3)
 
     # end to end through the C-ABI: one pic_step per step plus the field
@@ -323,69 +387,32 @@ def run_ours(args):
         pic.pic_step(g.h, 1)
         g.diag("field_energy")
     t1 = time.perf_counter()
-    pushed_e = g.info()["pushed"] - pushed_e0
-    te, pe = reduce_over_ranks(t1 - t0, pushed_e, ws)
-    e2e = pe / te
+    te, pe = reduce_over_ranks(t1 - t0, g.info()["pushed"] - pushed_e0, ws)
 
     peaks, src = _peaks()
-    k2_ms = timing["ms"]["gather_push_deposit"]
     k2_n = max(timing["launches"]["gather_push_deposit"], 1)
-    per_launch_pushes = (info["pushed"] - pushed0) / k2_n
-    avg_s = k2_ms / 1e3 / k2_n
-    sm_clock = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    achieved = FLOP_PER_PARTICLE * per_launch_pushes / avg_s / 1e12 if avg_s > 0 else 0.0
-    peak = _fp_peak_tflops(precision, peaks.get("sm_max_mhz", 2070.0))
-    roofline = {"kernel": "k_push_tiled (gather + Boris + Esirkepov deposit)",
-                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None,
-                "traffic": NCU_TRAFFIC_PER_PARTICLE[precision] * per_launch_pushes,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per particle "
-                                  "(plasma-filled 256x128x128 capture) x particles per launch",
-                "peak_source": "derived: 152 SMs x %s FMA lanes x 2 flop x %.0f MHz max clock" % (
-                    "128 FP32" if precision == "fp32" else "2 FP64", peaks.get("sm_max_mhz", 2070.0)),
-                "hbm_achieved_gbs": BYTES_PER_PARTICLE[precision] * per_launch_pushes / avg_s / 1e9
-                if avg_s > 0 else None,
-                "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": src,
-                "group_ms_per_step": {k: v / args.steps for k, v in timing["ms"].items()}}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32",
-            "data": "synthetic", "config": dict(_describe(cfg, start, precision, pre), tile=list(tile)),
-            "particles": info["np"], "roofline": roofline, "clocks": clk,
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32,
+    roof = _roofline(precision, pushed_local / k2_n, timing["ms"]["gather_push_deposit"] / 1e3 / k2_n,
+                     cfg["ppc"], peaks, src, timing["ms"], args.steps)
+    g.close()
+    return {"value": value, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "dtype": "f64" if precision == "fp64" else "f32",
+            "config": dict(_describe(cfg, start, precision, pre), tile=list(tile)),
+            "particles": info["np"], "roofline": roof, "clocks": clk,
+            "e2e": {"value": pe / te, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32,
                     "note": "pic_step(1) + pic_diag(field energy) into a host buffer per step; "
                             "the state is device-resident, a step uploads no input"},
             "gpu_launches": timing["kernels"]}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        from oracle import build as ob
-        ob.build()
-        r, desc, _ = _oracle_sample_rate()
-        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    g.close()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
 
 
-def run_batch(args):
+def batch_leg(args, rank, local, ws):
     """c3: N uneven FP32 instances (a0, density, waist, grid scan) advanced
     together, one CUDA graph launch per step; tile shapes autotuned."""
-    import torch
-    from paper_1204_0838_gb300 import build as pb
     from paper_1204_0838_gb300 import pic, workloads as W
-
-    ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
-    torch.cuda.set_device(local)
-    pb.build()
-    start = args.start_step if args.start_step >= 0 else 450
+    start = args.start_step if (args.start_step >= 0 and args.config == "c3") else 450
     cfgs = W.batch_configs(args.instances, seed=W.DEFAULT_SEED + 1000 * rank)
     sims, tiles = [], []
     pushed_k2 = k2_ms = 0.0
+    k2_launches = 0
     cache = os.environ.get("PIC_AUTOTUNE_CACHE", "/tmp/pic_autotune_%d.json" % os.getpid())
     for c in cfgs:
         c = dict(c)
@@ -406,6 +433,7 @@ def run_batch(args):
         t = pic.pic_timing_read(g.h)
         pic.pic_timing_start(g.h, False)
         k2_ms += t["ms"]["gather_push_deposit"]
+        k2_launches += t["launches"]["gather_push_deposit"]
         pushed_k2 += g.info()["pushed"] - p0
         sims.append(g)
     b = pic.pic_batch_create([g.h for g in sims])
@@ -413,15 +441,12 @@ def run_batch(args):
     p0 = sum(g.info()["pushed"] for g in sims)
     clocks = Clocks(local)
     clocks.start()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    _barrier(ws)
     g0 = pic.pic_batch_info(b)["graph_launches"]
     k0 = pic.pic_batch_info(b)["kernel_launches"]
     pic.pic_batch_step(b, args.steps)
     info = pic.pic_batch_info(b)
-    if ws > 1:
-        dist.barrier()
+    _barrier(ws)
     clk = clocks.stop()
     ms = info["last_step_ms"]
     pushed = sum(g.info()["pushed"] for g in sims) - p0
@@ -432,39 +457,78 @@ def run_batch(args):
     for _ in range(args.steps):
         pic.pic_batch_step(b, 1)
         pic.pic_batch_diag(b, 0, pic.PIC_DIAG_FIELD_ENERGY)
-    e2e = (sum(g.info()["pushed"] for g in sims) - pe0) / (time.perf_counter() - t0)
+    te, pe = reduce_over_ranks(time.perf_counter() - t0, sum(g.info()["pushed"] for g in sims) - pe0, ws)
     peaks, src = _peaks()
-    achieved = FLOP_PER_PARTICLE * pushed_k2 / (k2_ms / 1e3) / 1e12 if k2_ms > 0 else 0.0
-    peak = _fp_peak_tflops("fp32", peaks.get("sm_max_mhz", 2070.0))
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "c3: %d FP32 instances, a0 U[2,5], n U[0.003,0.02] n_c, waist "
-                                   "U[10,20] um, nx 256..768 x ny=nz 64..128, dx=lambda0/16, "
-                                   "dy=dz=lambda0/3, 1-2 ppc, window at c, steps %d.. of 500; one "
-                                   "CUDA graph launch per step; autotuned tiles" % (len(sims), start),
-                       "state": "each member loaded at rest at step %d - min(%d, nx) and run up to step %d "
-                                "(untimed): the run's own state" % (start, start, start) if not args.cold_start
-                       else "plasma loaded at rest at step %d (cold start)" % start,
-                       "tiles": tiles, "cells": int(sum(c["nx"] * c["ny"] * c["nz"] for c in cfgs)),
-                       "l2": "inputs larger than L2, no flush"},
-            "particles": int(sum(g.info()["np"] for g in sims)),
-            "roofline": {"kernel": "k_push_tiled (FP32), one host-driven step per member",
-                         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak if peak else None,
-                         "traffic": None,  # no capture of these member shapes (1-2 ppc, other cells)
-                         "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x max clock"},
-            "clocks": clk,
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8,
-                    "note": "pic_batch_step(1) + pic_batch_diag(field energy of instance 0) per step"},
-            "gpu_launches": info["kernel_launches"] - k0,
-            "graph_launches": info["graph_launches"] - g0}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    ppc_mean = sum(c["ppc"] for c in cfgs) / len(cfgs)
+    roof = _roofline("fp32", pushed_k2, k2_ms / 1e3, ppc_mean, peaks, src, {}, 1)
+    roof["kernel"] = "k_push_tiled (FP32), one host-driven step per member, summed over members"
+    roof["traffic"] = None  # no capture of these member shapes (1-2 ppc, dx = lambda0/16)
+    roof["traffic_source"] = "no capture of the batch members' shapes"
+    out = {"value": value, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "dtype": "f32",
+           "config": {"workload": "c3: %d FP32 instances, a0 U[2,5], n U[0.003,0.02] n_c, waist "
+                                  "U[10,20] um, nx 256..768 x ny=nz 64..128, dx=lambda0/16, "
+                                  "dy=dz=lambda0/3, 1-2 ppc, window at c, steps %d.. of 500; one "
+                                  "CUDA graph launch per step; autotuned tiles" % (len(sims), start),
+                      "state": "each member loaded at rest at step %d - min(%d, nx) and run up to step %d "
+                               "(untimed): the run's own state" % (start, start, start) if not args.cold_start
+                      else "plasma loaded at rest at step %d (cold start)" % start,
+                      "tiles": [list(t) for t in tiles],
+                      "cells": int(sum(c["nx"] * c["ny"] * c["nz"] for c in cfgs)),
+                      "l2": "inputs larger than L2, no flush"},
+           "particles": int(sum(g.info()["np"] for g in sims)),
+           "roofline": roof, "clocks": clk,
+           "e2e": {"value": pe / te, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8,
+                   "note": "pic_batch_step(1) + pic_batch_diag(field energy of instance 0) per step"},
+           "gpu_launches": info["kernel_launches"] - k0,
+           "graph_launches": info["graph_launches"] - g0}
     pic.pic_batch_destroy(b)
     for g in sims:
         g.close()
+    return out
+
+
+def _barrier(ws):
     if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_ours(args):
+    import torch
+    from paper_1204_0838_gb300 import build as pb
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    pb.build()
+    main = batch_leg(args, rank, local, ws) if args.config == "c3" else single_leg(args, args.config, rank, local, ws)
+    legs = {}
+    if args.config == "c1" and args.legs:
+        for name in args.legs.split(","):
+            legs[name] = batch_leg(args, rank, local, ws) if name == "c3" else single_leg(args, name, rank, local,
+                                                                                          ws)
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": main["dtype"], "data": "synthetic",
+            "config": main["config"], "particles": main["particles"], "roofline": main["roofline"],
+            "clocks": main["clocks"], "e2e": main["e2e"], "gpu_launches": main["gpu_launches"]}
+    if "graph_launches" in main:
+        line["graph_launches"] = main["graph_launches"]
+    if legs:
+        line["legs"] = legs
+        for name, key in (("c2", "fp32_over_fp64"), ("c3", "batched_over_fp64")):
+            if name in legs:
+                line[key] = legs[name]["value"] / main["value"]
+        line["gpu_launches"] = main["gpu_launches"] + sum(l["gpu_launches"] for l in legs.values())
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
 
 
@@ -472,8 +536,6 @@ def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.config == "c3":
-        run_batch(args)
     else:
         run_ours(args)
 

@@ -28,6 +28,11 @@ def config(name, crop=None, start_step=0):
         waist 16 um, window at c, 1000 steps, FP64.
     c2: c1 in FP32.
     c4: 2048x256x256, dx = lambda0/32, 4 ppc, 5000 steps, FP32.
+    inj: a dense window in which the wake traps electrons early: the c1
+        spacings on 384x96x96 cells, n = 0.03 n_c after a 10 um linear
+        up-ramp, a0 = 5, waist 4 um, 15 fs, 2 ppc lattice, window at c, FP64;
+        by step 5000 a few nC sit above gamma 20 (the injected charge of
+        Table 1 needs such a state; c1/c2 at 1000 steps have none).
     crop=(nx, ny, nz) keeps the spacings and physics on a smaller box.
     start_step=S places the window (and the laser with it) where it is after S
     steps of the run, with the plasma that has entered by then loaded cold.
@@ -52,6 +57,13 @@ def config(name, crop=None, start_step=0):
                    window=(1.0, 0.0), prof_x=[0.0, 50e-6, 1.0], prof_n=[0.0, 0.004, 0.004],
                    ppc=ppc, loading="lattice", a0=4.0, waist=16e-6, fwhm=fwhm, x_focus=0.0,
                    t_peak=2 * fwhm, steps=steps)
+    elif name == "inj":
+        nx, ny, nz, dx = 384, 96, 96, lam / 24
+        fwhm = 15e-15
+        cfg = dict(nx=nx, ny=ny, nz=nz, dx=dx, dy=lam / 3, dz=lam / 3, lambda0=lam, x0=-nx * dx,
+                   periodic_x=False, precision="fp64", seed=DEFAULT_SEED, window=(1.0, 0.0),
+                   prof_x=[0.0, 10e-6, 1.0], prof_n=[0.0, 0.03, 0.03], ppc=2, loading="lattice",
+                   a0=5.0, waist=4e-6, fwhm=fwhm, x_focus=0.0, t_peak=2 * fwhm, steps=5000)
     else:
         raise KeyError(name)
     if crop is not None:
