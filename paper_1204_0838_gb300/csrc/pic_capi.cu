@@ -558,6 +558,7 @@ int check_device_error(pic_t* h) {
     return fail(h, PIC_ERR_CAPACITY, "particle capacity exceeded during loading/injection");
   }
   if (ctrl[2] & 6) return fail(h, PIC_ERR_STATE, "tile bookkeeping error in the particle binning");
+  if (ctrl[2] & 16) return fail(h, PIC_ERR_STATE, "a tile held 2^20 or more particles (FP32 current tile range)");
   if (ctrl[2] & 8) {
     // reported once: the offending particles were absorbed
     const int zero = 0;

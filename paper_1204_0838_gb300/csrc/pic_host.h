@@ -149,7 +149,8 @@ void basic_diag_launch(pic_t* h, int kind, size_t len, const pic_diag_args* a, d
     default:  // CHARGE, SPECTRUM
       if (h->capacity > 0) {
         counted(h, G_OTHER);
-        k_particle_diag<T><<<grid_for(h->capacity, 256, 152 * 8), 256, 0, h->stream>>>(
+        const size_t smem = kind == PIC_DIAG_SPECTRUM && len <= (size_t)kDiagSharedBins ? len * sizeof(double) : 0;
+        k_particle_diag<T><<<grid_for(h->capacity, 256, 152 * 8), 256, smem, h->stream>>>(
             parts<T>(h, h->cur), h->d_ctrl + h->cur, kind == PIC_DIAG_SPECTRUM ? 1 : 0, a->gamma_min,
             diag_units(h).mc2_mev, a->e_min, a->e_max, (int)len, scratch);
       }

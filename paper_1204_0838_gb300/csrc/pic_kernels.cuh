@@ -736,31 +736,46 @@ __global__ void __launch_bounds__(256) k_gauss_residual(Geom<T> g, Fields<T> f, 
 }
 
 // kind 0: sum of w over gamma > gmin into out[0]; kind 1: histogram of
-// (gamma - 1) * mc2 over [e0, e1) into nb bins.
+// (gamma - 1) * mc2 over [e0, e1) into nb bins, accumulated per block in
+// shared memory (dynamic, nb doubles) when nb <= kDiagSharedBins, then added
+// to out once per nonzero bin.
+constexpr int kDiagSharedBins = 4096;
 template <typename T>
 __global__ void __launch_bounds__(256) k_particle_diag(Parts<T> p, const int* __restrict__ d_np, int kind,
                                                       double gmin, double mc2, double e0, double e1, int nb,
                                                       double* out) {
+  extern __shared__ double sbins[];
+  const bool local = kind == 1 && nb <= kDiagSharedBins;
+  if (local) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) sbins[b] = 0.0;
+    __syncthreads();
+  }
   const int n = *d_np;
   double acc = 0.0;
+  // gamma and the bin in the particles' own precision; the sums in FP64
+  const T te0 = (T)e0, te1 = (T)e1, tmc2 = (T)mc2;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    const double ux = p.u[0][q], uy = p.u[1][q], uz = p.u[2][q];
-    const double gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+    const T ux = p.u[0][q], uy = p.u[1][q], uz = p.u[2][q];
+    const T gam = sqrt(T(1) + ux * ux + uy * uy + uz * uz);
     const double w = (double)p.w[q];
     if (kind == 0) {
-      if (gam > gmin) acc += w;
+      if ((double)gam > gmin) acc += w;
     } else {
-      const double e = (gam - 1.0) * mc2;
-      if (e >= e0 && e < e1) {
-        int b = (int)floor((e - e0) / (e1 - e0) * nb);
+      const T e = (gam - T(1)) * tmc2;
+      if (e >= te0 && e < te1) {
+        int b = (int)floor((e - te0) / (te1 - te0) * (T)nb);
         if (b >= nb) b = nb - 1;
-        atomicAdd(out + b, w);
+        atomicAdd(local ? sbins + b : out + b, w);
       }
     }
   }
   if (kind == 0) {
     acc = block_sum(acc);
     if (threadIdx.x == 0) atomicAdd(out, acc);
+  } else if (local) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+      if (sbins[b] != 0.0) atomicAdd(out + b, sbins[b]);
   }
 }
 

@@ -432,6 +432,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom
     for (int i = threadIdx.x; i < 3 * nJ; i += blockDim.x) jt.f[i] = T(0);
   }
   if (threadIdx.x == 0) atomicAdd(pushed, (unsigned long long)(pend - pbeg));
+  // the fixed-point low words hold up to 2^20 contributions each
+  if (LaneLayout<T>::fixed_j && threadIdx.x == 0 && pend - pbeg >= (1 << 20)) atomicOr(err, 16);
   __syncthreads();
   const int ntile = pend - pbeg;
 

@@ -27,7 +27,8 @@ def config(name, crop=None, start_step=0):
         50 um linear up-ramp from x = 0, 2 ppc jittered lattice, a0 = 4, 30 fs,
         waist 16 um, window at c, 1000 steps, FP64.
     c2: c1 in FP32.
-    c4: 2048x256x256, dx = lambda0/32, 4 ppc, 5000 steps, FP32.
+    c4: 2048x256x256, dx = lambda0/32, 4 ppc, 5000 steps, FP32, injected-charge and
+        electron-spectrum diagnostics every 250 steps.
     inj: a dense window in which the wake traps electrons early: the c1
         spacings on 384x96x96 cells, n = 0.03 n_c after a 10 um linear
         up-ramp, a0 = 5, waist 4 um, 15 fs, 2 ppc lattice, window at c, FP64;
@@ -57,6 +58,8 @@ def config(name, crop=None, start_step=0):
                    window=(1.0, 0.0), prof_x=[0.0, 50e-6, 1.0], prof_n=[0.0, 0.004, 0.004],
                    ppc=ppc, loading="lattice", a0=4.0, waist=16e-6, fwhm=fwhm, x_focus=0.0,
                    t_peak=2 * fwhm, steps=steps)
+        if name == "c4":
+            cfg["diag_every"] = 250  # injected charge and electron spectrum
     elif name == "inj":
         nx, ny, nz, dx = 384, 96, 96, lam / 24
         fwhm = 15e-15
