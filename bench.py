@@ -45,7 +45,7 @@ ALG_BYTES_PER_PARTICLE = {"fp64": lambda ppc: 112 + 72 / ppc, "fp32": lambda ppc
 # of the current kernel on a 256x128x128 window in a run's own state (run for
 # 256 steps past a load at rest), 8x8x8 tiles; traffic per launch scales with
 # the particles processed.
-NCU_TRAFFIC_PER_PARTICLE = {"fp64": (808.351488e6 + 518.660096e6) / 8336282, "fp32": (420.643328e6 + 273.170688e6) / 8336282}
+NCU_TRAFFIC_PER_PARTICLE = {"fp64": (808.351488e6 + 518.660096e6) / 8336282, "fp32": (419.570688e6 + 273.255168e6) / 8336282}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per particle (c1 spacings, 256x128x128 "
                   "window in a run's state) x particles per launch")
 LIMITER = {"fp64": "FP64 pipe (ncu: ~84 % busy; DRAM < 1 %)",

@@ -471,7 +471,7 @@ int step_tiled(pic_t* h) {
     GroupTimer tm(h, G_PUSH);
     counted(h, G_PUSH);
     const T hq = (T)(h->q * h->dt / (2.0 * h->m));
-    k_push_tiled<T><<<tl.n, 256, tiled_smem_bytes<T>(tl), h->stream>>>(
+    k_push_tiled<T><<<tl.n, push_threads<T>(), tiled_smem_bytes<T>(tl), h->stream>>>(
         geom<T>(h), tl, f, parts<T>(h, h->cur), h->tstart[h->cur], (int)h->capacity, h->keys, h->tcnt, hq,
         (T)h->q, origin_after, x_lo(h), x_hi(h), h->d_pushed, h->d_ctrl + 2);
     CK(h, cudaGetLastError());
@@ -1701,7 +1701,7 @@ int enqueue_step_dyn(pic_t* h, cudaStream_t s, int cur, long long* kernels) {
   CK(h, cudaMemsetAsync(h->tcnt, 0, sizeof(int) * tl.n, s));
   k_step_begin<<<1, 32, 0, s>>>(h->d_dyn);
   const T hq = (T)(h->q * h->dt / (2.0 * h->m));
-  k_push_tiled<T><<<tl.n, 256, tiled_smem_bytes<T>(tl), s>>>(g, tl, f, parts<T>(h, cur), h->tstart[cur],
+  k_push_tiled<T><<<tl.n, push_threads<T>(), tiled_smem_bytes<T>(tl), s>>>(g, tl, f, parts<T>(h, cur), h->tstart[cur],
                                                             (int)h->capacity, h->keys, h->tcnt, hq, (T)h->q, 0,
                                                             x_lo(h), x_hi(h), h->d_pushed, h->d_ctrl + 2);
   k_e_update<T><<<e_update_grid(h), e_update_block(h), 0, s>>>(g, f, curl_view<T>(h), fc, pml_view<T>(h));

@@ -752,8 +752,12 @@ __global__ void __launch_bounds__(256) k_particle_diag(Parts<T> p, const int* __
   }
   const int n = *d_np;
   double acc = 0.0;
-  // gamma and the bin in the particles' own precision; the sums in FP64
+  // gamma and the bin in the particles' own precision; the sums in FP64.  A
+  // thread adds a run of particles that fall in the same bin before touching
+  // the histogram: most particles of a plasma sit in the lowest bin, where the
+  // lanes of a warp would otherwise all add to one address.
   const T te0 = (T)e0, te1 = (T)e1, tmc2 = (T)mc2;
+  int run_b = -1;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     const T ux = p.u[0][q], uy = p.u[1][q], uz = p.u[2][q];
     const T gam = sqrt(T(1) + ux * ux + uy * uy + uz * uz);
@@ -765,10 +769,16 @@ __global__ void __launch_bounds__(256) k_particle_diag(Parts<T> p, const int* __
       if (e >= te0 && e < te1) {
         int b = (int)floor((e - te0) / (te1 - te0) * (T)nb);
         if (b >= nb) b = nb - 1;
-        atomicAdd(local ? sbins + b : out + b, w);
+        if (b != run_b) {
+          if (run_b >= 0) atomicAdd(local ? sbins + run_b : out + run_b, acc);
+          run_b = b;
+          acc = 0.0;
+        }
+        acc += w;
       }
     }
   }
+  if (kind == 1 && run_b >= 0) atomicAdd(local ? sbins + run_b : out + run_b, acc);
   if (kind == 0) {
     acc = block_sum(acc);
     if (threadIdx.x == 0) atomicAdd(out, acc);

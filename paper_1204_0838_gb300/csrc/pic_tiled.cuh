@@ -360,12 +360,20 @@ __device__ __forceinline__ int push_particle(const Geom<T>& g, const Tiles& tl, 
   return key;
 }
 
+// Threads per CTA of the push: FP32 256 (the cell-round order is built for
+// 256 threads; two CTAs of about 100 KB of shared memory per SM); FP64 256
+// (one CTA per SM: the FP64 tile takes most of the shared memory).
+template <typename T>
+constexpr int push_threads() {
+  return 256;
+}
+
 // One CTA per tile.  keys[p] receives the particle's tile after the move (or
 // -1 when it leaves the open-x range once the window has moved to
 // origin_after); cnt_next[tile] counts the particles each tile will hold.
-// blockDim.x is 256.
+// blockDim.x is push_threads<T>().
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_push_tiled(Geom<T> g, Tiles tl, Fields<T> f, Parts<T> p,
+__global__ void __launch_bounds__(push_threads<T>(), sizeof(T) == 8 ? 1 : 2) k_push_tiled(Geom<T> g, Tiles tl, Fields<T> f, Parts<T> p,
                                                    const int* __restrict__ tstart, int capacity,
                                                    int* __restrict__ keys, int* __restrict__ cnt_next,
                                                    T h, T q, int origin_after, int xlo, int xhi,

@@ -1,5 +1,6 @@
-"""FP32 against FP64 on a state with injected electrons (north-star
-precision pattern; Sec. 3.2, Table 1 reports the injected charge).
+"""FP32 against FP64 on a state with injected electrons (FP32 fields,
+momenta, offsets and currents with FP64 reductions; Sec. 3.2, Table 1
+reports the injected charge).
 
 The c1/c2 runs carry no charge above gamma 20 in their first 1000 steps (the
 window is still in the density up-ramp), which makes a charge gate there
