@@ -69,10 +69,6 @@ struct JTile {
   int nJ, JY, JZ;
 };
 
-// x rounded to the nearest integer, for |x| < 2^22 (the float 1.5 * 2^23
-// puts the integer part in the low mantissa bits).
-__device__ __forceinline__ int round_small(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
-
 __device__ __forceinline__ void red_u32(unsigned* a, unsigned v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(a)), "r"(v) : "memory");
 }
@@ -284,18 +280,19 @@ __device__ __forceinline__ int push_particle(const Geom<T>& g, const Tiles& tl, 
     const int sm_ = st[comp], sb_ = st[ab], sc_ = st[ac];
     const int nm = nw[comp] - 1, nb = nw[ab], nc = nw[ac];
     if constexpr (LaneLayout<T>::fixed_j) {
-      // P[m] with a per-particle exponent kp (|P 2^kp| in [2^21, 2^22)), A
-      // with 2^21; their product carries 2^(kp + 21), shifted to the tile's
-      // 2^s with rounding to nearest
+      // P[m] as integers with a per-particle exponent kp (|P 2^kp| in
+      // [2^23, 2^24): the float's 24 significant bits, exactly), A with 2^30
+      // (exact for A >= 2^-7, within 2^-31 below); their product carries
+      // 2^(kp + 30), shifted to the tile's 2^s with rounding to nearest
       const float pmax = fmaxf(fmaxf(fabsf(P[0]), fabsf(P[1])), fmaxf(fabsf(P[2]), fabsf(P[3])));
       const int ep = ((__float_as_int(pmax) >> 23) & 255) - 127;
       if (ep > -100) {  // else the particle carries no current along this axis (or below 2^-100)
-        const int kp = 21 - ep;
+        const int kp = 23 - ep;
         const float sp = __int_as_float((127 + kp) << 23);
         int Pi[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) Pi[m] = round_small(P[m] * sp);
-        const int sh = min(max(kp + 21 - jt.s[comp], 0), 62);
+        for (int m = 0; m < 4; ++m) Pi[m] = __float2int_rn(P[m] * sp);
+        const int sh = min(max(kp + 30 - jt.s[comp], 0), 62);
         const long long half = (1LL << sh) >> 1;
 #pragma unroll
         for (int b = 0; b < 5; ++b) {
@@ -304,7 +301,7 @@ __device__ __forceinline__ int push_particle(const Geom<T>& g, const Tiles& tl, 
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
               if (c < nc) {
-                const int Ai = round_small((sb * ak[c] + db * bk[c]) * 2097152.0f);
+                const int Ai = __float2int_rn((sb * ak[c] + db * bk[c]) * 1073741824.0f);
 #pragma unroll
                 for (int m = 0; m < 4; ++m)
                   if (m < nm) {

@@ -365,6 +365,28 @@ def test_batched_equals_single_fp32():
 # ---------------------------------------------------------------------------
 # error behaviour of the C-ABI (host-side checks; nothing faults the GPU)
 # ---------------------------------------------------------------------------
+def test_fp32_tile_beyond_fixed_point_range_is_reported(monkeypatch):
+    """The FP32 current tile adds each contribution's low 12 bits into 32-bit
+    words, exact for fewer than 2^20 contributions to a node: a tile holding
+    2^20 particles or more reports PIC_ERR_STATE instead of a silently wrapped
+    current (host-side error word; nothing faults)."""
+    monkeypatch.setenv("PIC_TILE", "16,8,8")
+    shape = (16, 8, 8)
+    g = pic.Sim(*shape, LAM / 8, LAM / 3, LAM / 2, LAM, periodic_x=True, precision="fp32",
+                max_particles=(1 << 20) + 16)
+    n = (1 << 20) + 8
+    rng = np.random.default_rng(3)
+    xi = np.stack([rng.uniform(0, s, n) for s in shape])
+    u = rng.uniform(-0.1, 0.1, (3, n))
+    w = np.full(n, 1e-4)
+    g.set_particles(xi, u, w)
+    with pytest.raises(pic.PicError) as e:
+        g.step(1)
+    assert e.value.code == -7
+    assert "2^20" in str(e.value)
+    g.close()
+
+
 def test_error_codes():
     with pytest.raises(pic.PicError) as e:
         pic.Sim(32, 8, 8, LAM / 2, LAM / 4, LAM / 2, LAM)  # dx > dy violates Sec. 2
