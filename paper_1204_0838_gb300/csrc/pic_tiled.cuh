@@ -5,6 +5,7 @@
 // sort by tile (count fused into the push, scan, scatter).
 #pragma once
 
+#include "pic_fixed64.cuh"
 #include "pic_kernels.cuh"
 
 namespace pic {
@@ -39,33 +40,64 @@ __host__ __device__ __forceinline__ int jtile_n(const Tiles& tl) { return (tl.tx
 //   contributions.  The resolution 2^-s is about 2^-42 B, far below the FP32
 //   rounding of the contributions themselves, and the tile sum is exact and
 //   independent of the order of the adds.
+// FP64 push: the gather and the deposit run in 64-bit fixed point on the
+// integer pipes (pic_fixed64.cuh).  The staged E/B become int64 at a power of
+// two 2^sF per tile and component with max|F| 2^sF < 2^60, and the J tile
+// holds exact 64-bit sums as (high, low) 32-bit word pairs at 2^s per tile
+// and component with B 2^s < 2^62, B a bound on every node's sum taken from
+// the particles' speeds before the push (j_scale): a cold or slow tile gets
+// a fine scale, not one sized for moves of a whole cell.  The resolutions,
+// 2^-60 of the tile's largest field and 2^-62 of B, are at the level of
+// FP64 rounding at those scales, and the deposit's products round without
+// bias, so that thousands of contributions to a node add up no drift.
 constexpr int kRounds = 32;
 constexpr int kOrderChunk = 2048;
 constexpr int kFixedLoBits = 12;
 constexpr int kFixedRange = 42;
+constexpr int kFixed64Range = 60;   // staged fields: 4-term sums need |x| < 2^60
+constexpr int kFixed64JRange = 62;  // J sums of single products
+constexpr long long kThird62 = 1537228672809129301LL;  // round(2^62 / 3)
 template <typename T>
 struct LaneLayout {
   static constexpr bool cell_rounds = sizeof(T) == 4;
-  static constexpr bool fixed_j = sizeof(T) == 4;
+  static constexpr bool fixed_j = sizeof(T) == 4;   // FP32 J words: 12-bit low part
+  static constexpr bool fixed64 = sizeof(T) == 8;   // FP64 fixed-point gather and J words
+  // shared ints after the J tile: [0, 3) J scales, FP32 3 weight sum, FP64
+  // [4, 10) field exponent maxima, [10, 16) field scales and [16, 18) the
+  // sums behind the J bounds
+  static constexpr int scale_ints = sizeof(T) == 8 ? 18 : 4;
 };
 
 template <typename T>
 size_t tiled_smem_bytes(const Tiles& tl) {
-  const size_t jword = LaneLayout<T>::fixed_j ? 8 : sizeof(T);
-  size_t b = sizeof(T) * 6 * (size_t)stage_n(tl) + jword * 3 * (size_t)jtile_n(tl);
+  size_t b = sizeof(T) * 6 * (size_t)stage_n(tl) + 8 * 3 * (size_t)jtile_n(tl);
   if (LaneLayout<T>::cell_rounds) b += 4 * ((size_t)tl.tx * tl.ty * tl.tz + 3 * kRounds) + 2 * (size_t)kOrderChunk;
-  if (LaneLayout<T>::fixed_j) b += 16;  // the three scale exponents and the weight sum
-  return b;
+  return b + 4 * LaneLayout<T>::scale_ints;
 }
 
-// The shared-memory J tile of one CTA: [3][nJ] values over the cells
-// [o3, o3 + t + 5) per axis, as T (FP64) or as fixed-point word pairs (FP32).
+// The J tile's scale exponent s for component threadIdx.x (< 3): B 2^s <
+// 2^range for the bound B = 1.001 |q| S / (dt d_b d_c) on every node, where
+// S bounds the sum over the tile's particles of |w| times the largest
+// running sum of the deposit (FP32: S = sum_p |w|, a move of up to one cell;
+// FP64: from each particle's speed bound).  1.001: margin over the float
+// rounding of the sums.
+template <typename T>
+__device__ __forceinline__ int j_scale(const Geom<T>& g, T q, float S, int range) {
+  const int c = threadIdx.x;
+  const T jcc = c == 0 ? g.dt * g.dy * g.dz : (c == 1 ? g.dt * g.dx * g.dz : g.dt * g.dx * g.dy);
+  const float B = 1.001f * fabsf((float)q) * S / (float)jcc;
+  const int eb = ((__float_as_int(B) >> 23) & 255) - 127;  // B in [2^eb, 2^(eb+1))
+  return B > 0.0f ? range - 1 - eb : 0;
+}
+
+// The shared-memory J tile of one CTA: [3][nJ] fixed-point word pairs over
+// the cells [o3, o3 + t + 5) per axis, and the tile's scales.
 template <typename T>
 struct JTile {
-  T* f;
   unsigned* hi;
   unsigned* lo;
-  const int* s;  // fixed point: scale exponent per component
+  const int* s;   // J scale exponent per component
+  const int* fs;  // FP64: staged field scale per component
   int nJ, JY, JZ;
 };
 
@@ -128,6 +160,88 @@ __device__ __forceinline__ bool lt_zero(float o) { return o < 0.0f; }
 __device__ __forceinline__ bool ge_one(float o) { return o >= 1.0f; }
 __device__ __forceinline__ bool lt_half(float o) { return o < 0.5f; }
 
+// FP64 Esirkepov deposit of one particle into the fixed-point J tile: old
+// cell lc (staged frame) with node weights wn, cell step dc and new offsets
+// o1, charge times weight qw (0 for a particle that does not deposit).
+template <typename T>
+__device__ __forceinline__ void deposit_fixed64(const JTile<T>& jt, const T jc[3], const int lc[3], const int dc[3],
+                                                const T wn[3][4], const T o1[3], double qw) {
+  int lw[3], nw[3];
+  // shape factors at 2^62, the factors A and bk and the running sums
+  // P 2^s of the current in 64-bit fixed point, exact 64-bit tile sums
+  long long S0i[3][5], DSi[3][5];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T w1[4];
+    bspline3(o1[d], w1);
+    long long wnI[4], w1i[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      wnI[k] = to_fixed(wn[d][k], 62);
+      w1i[k] = to_fixed(w1[k], 62);
+    }
+    const int p0 = dc[d] < 0 ? 1 : 0, p1 = dc[d] > 0 ? 1 : 0;
+    lw[d] = lc[d] - 1 - p0;
+    nw[d] = dc[d] != 0 ? 5 : 4;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const long long a0 = p0 ? (m > 0 ? wnI[m > 0 ? m - 1 : 0] : 0LL) : (m < 4 ? wnI[m < 4 ? m : 3] : 0LL);
+      const long long a1 = p1 ? (m > 0 ? w1i[m > 0 ? m - 1 : 0] : 0LL) : (m < 4 ? w1i[m < 4 ? m : 3] : 0LL);
+      S0i[d][m] = a0;
+      DSi[d][m] = a1 - a0;
+    }
+  }
+  const W62 third62 = w62(kThird62);
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp) {
+    const int ab = comp == 0 ? 1 : 0, ac = comp == 2 ? 1 : 2;
+    // P 2^s = q w jc run 2^s, below 2^62 by the choice of the tile's scale
+    // (|run| <= 3/4 |displacement| along comp)
+    const double cfs = qw * (double)jc[comp] * exp2i(jt.s[comp] - 62);
+    long long Pi[4];
+    long long run = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      run += DSi[comp][m];
+      Pi[m] = to_fixed(__ll2double_rn(run) * cfs, 0);
+    }
+    // ak = (S0 + S1)/2, bk = (S0 + 2 S1)/6 (the sum S0 + 2 S1 <= 2^63 is
+    // formed unsigned)
+    W62 akW[5], bkW[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      akW[c] = w62((2 * S0i[ac][c] + DSi[ac][c]) >> 1);
+      const unsigned long long t2 = 3ull * (unsigned long long)S0i[ac][c] + 2ull * (unsigned long long)DSi[ac][c];
+      bkW[c] = w62(fix_mul_c((long long)(t2 >> 1), third62));
+    }
+    const int st[3] = {jt.JY * jt.JZ, jt.JZ, 1};
+    const int base0 = comp * jt.nJ + lw[0] * st[0] + lw[1] * st[1] + lw[2] * st[2];
+    const int sm_ = st[comp], sb_ = st[ab], sc_ = st[ac];
+    const int nm = nw[comp] - 1, nb = nw[ab], nc = nw[ac];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      if (b < nb) {
+        const long long sb = S0i[ab][b], db = DSi[ab][b];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          if (c < nc) {
+            FixAcc acc = fix_init();
+            fix_mac_c(acc, sb, akW[c]);
+            fix_mac_c(acc, db, bkW[c]);
+            const W62 Aw = w62(max(fix_result(acc), 0LL));  // A >= 0; clamps a rounding below zero
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+              if (m < nm) {
+                const int idx = base0 + m * sm_ + b * sb_ + c * sc_;
+                add_fixed64(jt.hi + idx, jt.lo + idx, fix_mul_c(Pi[m], Aw));
+              }
+          }
+        }
+      }
+    }
+  }
+}
+
 // Gather, Boris push, move and Esirkepov deposit of particle pi of the tile
 // whose staged origin is o3; returns its destination tile key (-1: absorbed).
 template <typename T>
@@ -174,12 +288,31 @@ __device__ __forceinline__ int push_particle(const Geom<T>& g, const Tiles& tl, 
     bn[d] = lc[d] - 1;
     bh[d] = lc[d] - (lo ? 2 : 1);
   }
-  E[0] = gather_smem<4, 4, 4>(sF + 0 * nS, SY, SZ, bh[0], bn[1], bn[2], wh[0], wn[1], wn[2]);
-  E[1] = gather_smem<4, 4, 4>(sF + 1 * nS, SY, SZ, bn[0], bh[1], bn[2], wn[0], wh[1], wn[2]);
-  E[2] = gather_smem<4, 4, 4>(sF + 2 * nS, SY, SZ, bn[0], bn[1], bh[2], wn[0], wn[1], wh[2]);
-  B[0] = gather_smem<4, 4, 4>(sF + 3 * nS, SY, SZ, bn[0], bh[1], bh[2], wn[0], wh[1], wh[2]);
-  B[1] = gather_smem<4, 4, 4>(sF + 4 * nS, SY, SZ, bh[0], bn[1], bh[2], wh[0], wn[1], wh[2]);
-  B[2] = gather_smem<4, 4, 4>(sF + 5 * nS, SY, SZ, bh[0], bh[1], bn[2], wh[0], wh[1], wn[2]);
+  if constexpr (LaneLayout<T>::fixed64) {
+    // FP64: the weights at 2^62 on the fixed-point staged tile
+    const long long* sI = reinterpret_cast<const long long*>(sF);
+    W62 Wn[3][4], Wh[3][4];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Wn[d][k] = w62(to_fixed(wn[d][k], 62));
+        Wh[d][k] = w62(to_fixed(wh[d][k], 62));
+      }
+    E[0] = from_fixed(gather_fixed<4, 4, 4>(sI + 0 * nS, SY, SZ, bh[0], bn[1], bn[2], Wh[0], Wn[1], Wn[2]), jt.fs[0]);
+    E[1] = from_fixed(gather_fixed<4, 4, 4>(sI + 1 * nS, SY, SZ, bn[0], bh[1], bn[2], Wn[0], Wh[1], Wn[2]), jt.fs[1]);
+    E[2] = from_fixed(gather_fixed<4, 4, 4>(sI + 2 * nS, SY, SZ, bn[0], bn[1], bh[2], Wn[0], Wn[1], Wh[2]), jt.fs[2]);
+    B[0] = from_fixed(gather_fixed<4, 4, 4>(sI + 3 * nS, SY, SZ, bn[0], bh[1], bh[2], Wn[0], Wh[1], Wh[2]), jt.fs[3]);
+    B[1] = from_fixed(gather_fixed<4, 4, 4>(sI + 4 * nS, SY, SZ, bh[0], bn[1], bh[2], Wh[0], Wn[1], Wh[2]), jt.fs[4]);
+    B[2] = from_fixed(gather_fixed<4, 4, 4>(sI + 5 * nS, SY, SZ, bh[0], bh[1], bn[2], Wh[0], Wh[1], Wn[2]), jt.fs[5]);
+  } else {
+    E[0] = gather_smem<4, 4, 4>(sF + 0 * nS, SY, SZ, bh[0], bn[1], bn[2], wh[0], wn[1], wn[2]);
+    E[1] = gather_smem<4, 4, 4>(sF + 1 * nS, SY, SZ, bn[0], bh[1], bn[2], wn[0], wh[1], wn[2]);
+    E[2] = gather_smem<4, 4, 4>(sF + 2 * nS, SY, SZ, bn[0], bn[1], bh[2], wn[0], wn[1], wh[2]);
+    B[0] = gather_smem<4, 4, 4>(sF + 3 * nS, SY, SZ, bn[0], bh[1], bh[2], wn[0], wh[1], wh[2]);
+    B[1] = gather_smem<4, 4, 4>(sF + 4 * nS, SY, SZ, bh[0], bn[1], bh[2], wh[0], wn[1], wh[2]);
+    B[2] = gather_smem<4, 4, 4>(sF + 5 * nS, SY, SZ, bh[0], bh[1], bn[2], wh[0], wh[1], wn[2]);
+  }
 
   // relativistic Boris push
   T um[3], tv[3], sv[3];
@@ -238,48 +371,50 @@ __device__ __forceinline__ int push_particle(const Geom<T>& g, const Tiles& tl, 
   // there (node 5 of the window carries nothing): nw = 4 or 5 nodes, and
   // the running sum along the current's own axis vanishes on its last
   // node, so only nw - 1 current values are nonzero.
-  T S0[3][5], DS[3][5];
-  int lw[3], nw[3];
+  if constexpr (LaneLayout<T>::fixed64) {
+    deposit_fixed64(jt, jc, lc, dc, wn, o1, bad ? 0.0 : (double)q * (double)p.w[pi]);
+  } else {
+    int lw[3], nw[3];
+    T S0[3][5], DS[3][5];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    T w1[4];
-    bspline3(o1[d], w1);
-    const int p0 = dc[d] < 0 ? 1 : 0, p1 = dc[d] > 0 ? 1 : 0;
-    lw[d] = lc[d] - 1 - p0;
-    nw[d] = dc[d] != 0 ? 5 : 4;
+    for (int d = 0; d < 3; ++d) {
+      T w1[4];
+      bspline3(o1[d], w1);
+      const int p0 = dc[d] < 0 ? 1 : 0, p1 = dc[d] > 0 ? 1 : 0;
+      lw[d] = lc[d] - 1 - p0;
+      nw[d] = dc[d] != 0 ? 5 : 4;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      const T a0 = p0 ? (m > 0 ? wn[d][m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? wn[d][m < 4 ? m : 3] : T(0));
-      const T a1 = p1 ? (m > 0 ? w1[m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? w1[m < 4 ? m : 3] : T(0));
-      S0[d][m] = a0;
-      DS[d][m] = a1 - a0;
+      for (int m = 0; m < 5; ++m) {
+        const T a0 = p0 ? (m > 0 ? wn[d][m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? wn[d][m < 4 ? m : 3] : T(0));
+        const T a1 = p1 ? (m > 0 ? w1[m > 0 ? m - 1 : 0] : T(0)) : (m < 4 ? w1[m < 4 ? m : 3] : T(0));
+        S0[d][m] = a0;
+        DS[d][m] = a1 - a0;
+      }
     }
-  }
-  const T qw = bad ? T(0) : q * p.w[pi];
+    const T qw = bad ? T(0) : q * p.w[pi];
 #pragma unroll
-  for (int comp = 0; comp < 3; ++comp) {
-    // axis `comp` carries the running sum; (b, c) are the other two axes
-    const int ab = comp == 0 ? 1 : 0, ac = comp == 2 ? 1 : 2;
-    T P[4];
-    T run = T(0);
-    const T cf = qw * jc[comp];
+    for (int comp = 0; comp < 3; ++comp) {
+      // axis `comp` carries the running sum; (b, c) are the other two axes
+      const int ab = comp == 0 ? 1 : 0, ac = comp == 2 ? 1 : 2;
+      T P[4];
+      T run = T(0);
+      const T cf = qw * jc[comp];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      run += DS[comp][m];
-      P[m] = cf * run;
-    }
-    T ak[5], bk[5];
+      for (int m = 0; m < 4; ++m) {
+        run += DS[comp][m];
+        P[m] = cf * run;
+      }
+      T ak[5], bk[5];
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      ak[m] = S0[ac][m] + T(0.5) * DS[ac][m];
-      bk[m] = T(0.5) * S0[ac][m] + third * DS[ac][m];
-    }
-    // strides of the three axes in the J tile; (m, b, c) walk (comp, ab, ac)
-    const int st[3] = {jt.JY * jt.JZ, jt.JZ, 1};
-    const int base0 = comp * jt.nJ + lw[0] * st[0] + lw[1] * st[1] + lw[2] * st[2];
-    const int sm_ = st[comp], sb_ = st[ab], sc_ = st[ac];
-    const int nm = nw[comp] - 1, nb = nw[ab], nc = nw[ac];
-    if constexpr (LaneLayout<T>::fixed_j) {
+      for (int m = 0; m < 5; ++m) {
+        ak[m] = S0[ac][m] + T(0.5) * DS[ac][m];
+        bk[m] = T(0.5) * S0[ac][m] + third * DS[ac][m];
+      }
+      // strides of the three axes in the J tile; (m, b, c) walk (comp, ab, ac)
+      const int st[3] = {jt.JY * jt.JZ, jt.JZ, 1};
+      const int base0 = comp * jt.nJ + lw[0] * st[0] + lw[1] * st[1] + lw[2] * st[2];
+      const int sm_ = st[comp], sb_ = st[ab], sc_ = st[ac];
+      const int nm = nw[comp] - 1, nb = nw[ab], nc = nw[ac];
       // P[m] as integers with a per-particle exponent kp (|P 2^kp| in
       // [2^23, 2^24): the float's 24 significant bits, exactly), A with 2^30
       // (exact for A >= 2^-7, within 2^-31 below); their product carries
@@ -311,22 +446,6 @@ __device__ __forceinline__ int push_particle(const Geom<T>& g, const Tiles& tl, 
                     red_u32(jt.lo + idx, (unsigned)X & ((1u << kFixedLoBits) - 1u));
                   }
               }
-            }
-          }
-        }
-      }
-    } else {
-#pragma unroll
-      for (int b = 0; b < 5; ++b) {
-        if (b < nb) {
-          const T sb = S0[ab][b], db = DS[ab][b];
-#pragma unroll
-          for (int c = 0; c < 5; ++c) {
-            if (c < nc) {
-              const T A = sb * ak[c] + db * bk[c];
-#pragma unroll
-              for (int m = 0; m < 4; ++m)
-                if (m < nm) atomicAdd(jt.f + base0 + m * sm_ + b * sb_ + c * sc_, P[m] * A);
             }
           }
         }
@@ -391,50 +510,94 @@ __global__ void __launch_bounds__(push_threads<T>(), sizeof(T) == 8 ? 1 : 2) k_p
   jt.nJ = nJ;
   jt.JY = tl.ty + 5;
   jt.JZ = tl.tz + 5;
-  unsigned char* after_j;
-  int* sexp = nullptr;
-  if constexpr (LaneLayout<T>::fixed_j) {
-    jt.f = nullptr;
-    jt.hi = reinterpret_cast<unsigned*>(sm + 6 * nS);
-    jt.lo = jt.hi + 3 * nJ;
-    sexp = reinterpret_cast<int*>(jt.lo + 3 * nJ);
-    jt.s = sexp;
-    after_j = reinterpret_cast<unsigned char*>(sexp + 4);
-  } else {
-    jt.f = sm + 6 * nS;
-    jt.hi = jt.lo = nullptr;
-    jt.s = nullptr;
-    after_j = reinterpret_cast<unsigned char*>(jt.f + 3 * nJ);
-  }
+  jt.hi = reinterpret_cast<unsigned*>(sm + 6 * nS);
+  jt.lo = jt.hi + 3 * nJ;
+  int* sexp = reinterpret_cast<int*>(jt.lo + 3 * nJ);
+  jt.s = sexp;
+  jt.fs = sexp + 10;
+  unsigned char* after_j = reinterpret_cast<unsigned char*>(sexp + LaneLayout<T>::scale_ints);
 
-  // stage E and B (wrapped storage indices; see the ring note in pic_device.cuh)
+  // stage E and B (wrapped storage indices; see the ring note in pic_device.cuh);
+  // FP64 also takes the largest exponent of each component
+  int emax[6] = {0, 0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < nS; i += blockDim.x) {
     const int lz = i % SZ, r = i / SZ;
     const int ly = r % SY, lx = r / SY;
     const size_t gi = (size_t)wrapi(o3[0] + lx, g.nx) * g.nyz + (size_t)wrapi(o3[1] + ly, g.ny) * g.nz +
                       wrapi(o3[2] + lz, g.nz);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) sF[c * nS + i] = f.c[c][gi];
+    for (int c = 0; c < 6; ++c) {
+      const T v = f.c[c][gi];
+      sF[c * nS + i] = v;
+      if constexpr (LaneLayout<T>::fixed64)
+        emax[c] = max(emax[c], (int)((__double_as_longlong(v) >> 52) & 0x7FF));
+    }
   }
-  if constexpr (LaneLayout<T>::fixed_j) {
-    for (int i = threadIdx.x; i < 6 * nJ; i += blockDim.x) jt.hi[i] = 0u;
-    // the scale of the fixed-point tile: B = |q jc| sum_p w_p bounds every node
+  if (threadIdx.x < LaneLayout<T>::scale_ints) sexp[threadIdx.x] = 0;
+  __syncthreads();
+  if constexpr (LaneLayout<T>::fixed64) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const unsigned e = __reduce_max_sync(0xffffffffu, (unsigned)emax[c]);
+      if ((threadIdx.x & 31) == 0) atomicMax(sexp + 4 + c, (int)e);
+    }
+    __syncthreads();
+    // bound on each particle's speed after the push: |u'| <= |u| + 2 |h| |E|
+    // (the Boris rotation keeps |u|), |E| <= sqrt 3 max_c |E_c| < sqrt 3
+    // 2^(emax - 1022); sums of |w| min(1, bound) and of |w| over the tile
+    const int eE = max(max(sexp[4], sexp[5]), sexp[6]);
+    const float kick = eE == 0 ? 0.0f : ldexpf(3.4642f * fabsf((float)h), eE - 1022);
+    float su = 0.0f, sw = 0.0f;
+    for (int k = threadIdx.x; k < pend - pbeg; k += blockDim.x) {
+      const float wa = fabsf((float)p.w[pbeg + k]);
+      const float ux = (float)p.u[0][pbeg + k], uy = (float)p.u[1][pbeg + k], uz = (float)p.u[2][pbeg + k];
+      su += wa * fminf(1.0f, sqrtf(ux * ux + uy * uy + uz * uz) + kick);
+      sw += wa;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      su += __shfl_down_sync(0xffffffffu, su, o);
+      sw += __shfl_down_sync(0xffffffffu, sw, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(reinterpret_cast<float*>(sexp + 16), su);
+      atomicAdd(reinterpret_cast<float*>(sexp + 17), sw);
+    }
+  }
+  for (int i = threadIdx.x; i < 6 * nJ; i += blockDim.x) jt.hi[i] = 0u;
+  if constexpr (!LaneLayout<T>::fixed64) {
+    // the scale of the fixed-point J tile: B = |q jc| sum_p w_p bounds every node
     float ws = 0.0f;
     for (int k = threadIdx.x; k < pend - pbeg; k += blockDim.x) ws += fabsf((float)p.w[pbeg + k]);
     for (int o = 16; o > 0; o >>= 1) ws += __shfl_down_sync(0xffffffffu, ws, o);
-    if (threadIdx.x == 0) sexp[3] = 0;
-    __syncthreads();
     if ((threadIdx.x & 31) == 0) atomicAdd(reinterpret_cast<float*>(sexp + 3), ws);
-    __syncthreads();
-    if (threadIdx.x < 3) {
-      const T jcc = threadIdx.x == 0 ? g.dt * g.dy * g.dz : (threadIdx.x == 1 ? g.dt * g.dx * g.dz : g.dt * g.dx * g.dy);
-      // 1.001: margin over the float rounding of the sum
-      const float B = 1.001f * fabsf((float)q) * __int_as_float(sexp[3]) / (float)jcc;
-      const int eb = ((__float_as_int(B) >> 23) & 255) - 127;  // B in [2^eb, 2^(eb+1))
-      sexp[threadIdx.x] = B > 0.0f ? kFixedRange - 1 - eb : 0;
-    }
+  }
+  __syncthreads();
+  if constexpr (!LaneLayout<T>::fixed64) {
+    if (threadIdx.x < 3) sexp[threadIdx.x] = j_scale(g, q, __int_as_float(sexp[3]), kFixedRange);
   } else {
-    for (int i = threadIdx.x; i < 3 * nJ; i += blockDim.x) jt.f[i] = T(0);
+    // a particle moves at most dt/d |u'| cells along an axis, and a running
+    // sum of the deposit changes by at most 3/4 of the move (the slope bound
+    // of the cubic spline's partial sums); 2^-20 covers the rounding
+    if (threadIdx.x < 3) {
+      const int c = threadIdx.x;
+      const float dtd = (float)(g.dt / (c == 0 ? g.dx : (c == 1 ? g.dy : g.dz)));
+      const float S = 0.75f * (dtd * __int_as_float(sexp[16]) + 0x1p-20f * __int_as_float(sexp[17]));
+      sexp[c] = j_scale(g, q, S, kFixed64JRange);
+    }
+    // staged fields to int64 at 2^sF, max|F| 2^sF < 2^60 (an all-zero
+    // component takes sF = 1000; a non-finite value reports a numeric error)
+    int sfc[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const int e = sexp[4 + c];
+      sfc[c] = e == 0 ? 1000 : min(kFixed64Range - 1 - (e - 1023), 1000);
+      if (e == 0x7FF && threadIdx.x == 0) atomicOr(err, 8);
+    }
+    if (threadIdx.x < 6) sexp[10 + threadIdx.x] = sfc[threadIdx.x];
+    long long* sI = reinterpret_cast<long long*>(sF);
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      for (int i = threadIdx.x; i < nS; i += blockDim.x) sI[c * nS + i] = to_fixed(sF[c * nS + i], sfc[c]);
   }
   if (threadIdx.x == 0) atomicAdd(pushed, (unsigned long long)(pend - pbeg));
   // the fixed-point low words hold up to 2^20 contributions each
@@ -524,13 +687,14 @@ __global__ void __launch_bounds__(push_threads<T>(), sizeof(T) == 8 ? 1 : 2) k_p
   for (int i = threadIdx.x; i < 3 * nJ; i += blockDim.x) {
     const int comp = i / nJ, li = i - comp * nJ;
     T v;
-    if constexpr (LaneLayout<T>::fixed_j) {
+    if constexpr (LaneLayout<T>::fixed64) {
+      const long long X = (long long)(((unsigned long long)jt.hi[i] << 32) | jt.lo[i]);
+      if (X == 0) continue;
+      v = from_fixed(X, sexp[comp]);
+    } else {
       const long long X = (long long)(int)jt.hi[i] * (1LL << kFixedLoBits) + (long long)jt.lo[i];
       if (X == 0) continue;
       v = ldexpf((float)X, -sexp[comp]);
-    } else {
-      v = jt.f[i];
-      if (v == T(0)) continue;
     }
     const int lz = li % jt.JZ, r = li / jt.JZ;
     const int ly = r % jt.JY, lx = r / jt.JY;

@@ -90,6 +90,32 @@ def test_one_step_parity_random_state(periodic, shape, npart):
     compare_fields(g, o, 1e-10)
 
 
+def test_one_step_parity_zero_and_sparse_field_components():
+    """Components that are exactly zero everywhere, one that is non-zero on a
+    few slabs only, and values over a wide range in one tile (a subnormal,
+    1e-17, 1e3): the FP64 push stages each tile's fields as 64-bit fixed
+    point scaled to that tile's largest value, and must gather exact zeros as
+    zero and small fields to their own precision."""
+    shape = (32, 16, 16)
+    g, o = _pair(shape, False)
+    inf = o.info()
+    F, xi, u, w, ids = W.random_state(shape, 20000, 5, umax=1.0, periodic_x=False,
+                                      dV=inf["dx"] * inf["dy"] * inf["dz"])
+    rng = np.random.default_rng(9)
+    F[:6] = 0.0
+    F[1, 4] = 1.5e-17 * rng.standard_normal(shape[1:])
+    F[1, 12] = 1e3 * rng.standard_normal(shape[1:])
+    F[1, 13, 4, 5] = 5e-320
+    F[5, 20:22] = 1e-6 * rng.standard_normal((2,) + shape[1:])
+    for s in (g, o):
+        s.set_fields(F)
+        s.set_particles(xi, u, w, ids)
+    g.step(1)
+    o.step(1)
+    compare_particles(g.particles(), o.particles(), 1e-10)
+    compare_fields(g, o, 1e-10)
+
+
 @pytest.mark.parametrize("tile", ["5,3,3", "16,4,8", "1,1,1", "32,16,16"])
 def test_ragged_and_odd_tiles(tile, monkeypatch):
     monkeypatch.setenv("PIC_TILE", tile)
