@@ -45,10 +45,11 @@ ALG_BYTES_PER_PARTICLE = {"fp64": lambda ppc: 112 + 72 / ppc, "fp32": lambda ppc
 # of the current kernel on a 256x128x128 window in a run's own state (run for
 # 256 steps past a load at rest), 8x8x8 tiles; traffic per launch scales with
 # the particles processed.
-NCU_TRAFFIC_PER_PARTICLE = {"fp64": (808.351488e6 + 518.660096e6) / 8336282, "fp32": (419.570688e6 + 273.255168e6) / 8336282}
+NCU_TRAFFIC_PER_PARTICLE = {"fp64": (807.540480e6 + 525.361152e6) / 8336282, "fp32": (419.570688e6 + 273.255168e6) / 8336282}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per particle (c1 spacings, 256x128x128 "
                   "window in a run's state) x particles per launch")
-LIMITER = {"fp64": "FP64 pipe (ncu: ~84 % busy; DRAM < 1 %)",
+LIMITER = {"fp64": ("issue latency and instruction fetch (ncu: issue active 26 %, FP64 pipe 22 %, integer ALU "
+                    "22 %, 8 warps per SM, top stall no_instruction; DRAM ~1 %)"),
            "fp32": "shared-memory pipe (ncu: L1tex ~80 %; DRAM ~3 %)"}
 
 
@@ -320,8 +321,11 @@ def _roofline(precision, pushes_per_launch, avg_launch_s, ppc, peaks, src, group
             "frac": achieved / peak if peak else None,
             "traffic": per * pushes_per_launch if per else None,
             "traffic_source": TRAFFIC_SOURCE if per else "no capture of the current kernel",
-            "peak_source": "derived: 152 SMs x %s FMA lanes x 2 flop x %.0f MHz max clock" % (
-                "128 FP32" if precision == "fp32" else "2 FP64", peaks.get("sm_max_mhz", 2070.0)),
+            "peak_source": "derived: 152 SMs x %s FMA lanes x 2 flop x %.0f MHz max clock%s" % (
+                "128 FP32" if precision == "fp32" else "2 FP64", peaks.get("sm_max_mhz", 2070.0),
+                "" if precision == "fp32" else
+                " (the FP64 pipe's rate for the push's FP64 arithmetic; the push runs the gather and the "
+                "deposit in 64-bit fixed point on the integer pipes instead)"),
             "limiter": LIMITER[precision],
             "hbm_algorithmic_bytes_per_particle": alg,
             "hbm_achieved_gbs": hbm, "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": src,
