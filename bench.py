@@ -45,11 +45,11 @@ ALG_BYTES_PER_PARTICLE = {"fp64": lambda ppc: 112 + 72 / ppc, "fp32": lambda ppc
 # of the current kernel on a 256x128x128 window in a run's own state (run for
 # 256 steps past a load at rest), 8x8x8 tiles; traffic per launch scales with
 # the particles processed.
-NCU_TRAFFIC_PER_PARTICLE = {"fp64": (807.540480e6 + 525.361152e6) / 8336282, "fp32": (419.570688e6 + 273.255168e6) / 8336282}
+NCU_TRAFFIC_PER_PARTICLE = {"fp64": (860.888576e6 + 1019.139e6) / 8336282, "fp32": (419.570688e6 + 273.255168e6) / 8336282}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per particle (c1 spacings, 256x128x128 "
                   "window in a run's state) x particles per launch")
-LIMITER = {"fp64": ("issue latency and instruction fetch (ncu: issue active 26 %, FP64 pipe 22 %, integer ALU "
-                    "22 %, 8 warps per SM, top stall no_instruction; DRAM ~1 %)"),
+LIMITER = {"fp64": ("issue latency and instruction fetch (ncu: issue active 36 %, FP64 pipe 30 %, integer ALU "
+                    "27 %, 16 warps per SM, top stalls no_instruction 22 % and wait 19 % of samples; DRAM 2 %)"),
            "fp32": "shared-memory pipe (ncu: L1tex ~80 %; DRAM ~3 %)"}
 
 

@@ -192,17 +192,32 @@ __device__ __forceinline__ void deposit_fixed64(const JTile<T>& jt, const T jc[3
     }
   }
   const W62 third62 = w62(kThird62);
-#pragma unroll
+  const int st[3] = {jt.JY * jt.JZ, jt.JZ, 1};
+  const int base = lw[0] * st[0] + lw[1] * st[1] + lw[2] * st[2];
+  // one copy of the component's deposit in a loop over the three components
+  // (the unrolled copies overflow the instruction cache): the axes' factors
+  // are selected into comp-relative arrays, m along comp, b along ab, c
+  // along ac
+#pragma unroll 1
   for (int comp = 0; comp < 3; ++comp) {
-    const int ab = comp == 0 ? 1 : 0, ac = comp == 2 ? 1 : 2;
+    const bool c0 = comp == 0, c1 = comp == 1;
+    long long dsm[4], sb[5], db[5], sc[5], dsc[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      if (k < 4) dsm[k] = c0 ? DSi[0][k] : (c1 ? DSi[1][k] : DSi[2][k]);
+      sb[k] = c0 ? S0i[1][k] : S0i[0][k];  // ab = 1 for comp 0, else 0
+      db[k] = c0 ? DSi[1][k] : DSi[0][k];
+      sc[k] = comp == 2 ? S0i[1][k] : S0i[2][k];  // ac = 1 for comp 2, else 2
+      dsc[k] = comp == 2 ? DSi[1][k] : DSi[2][k];
+    }
     // P 2^s = q w jc run 2^s, below 2^62 by the choice of the tile's scale
     // (|run| <= 3/4 |displacement| along comp)
-    const double cfs = qw * (double)jc[comp] * exp2i(jt.s[comp] - 62);
+    const double cfs = qw * (double)(c0 ? jc[0] : (c1 ? jc[1] : jc[2])) * exp2i(jt.s[comp] - 62);
     long long Pi[4];
     long long run = 0;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      run += DSi[comp][m];
+      run += dsm[m];
       Pi[m] = to_fixed(__ll2double_rn(run) * cfs, 0);
     }
     // ak = (S0 + S1)/2, bk = (S0 + 2 S1)/6 (the sum S0 + 2 S1 <= 2^63 is
@@ -210,24 +225,22 @@ __device__ __forceinline__ void deposit_fixed64(const JTile<T>& jt, const T jc[3
     W62 akW[5], bkW[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      akW[c] = w62((2 * S0i[ac][c] + DSi[ac][c]) >> 1);
-      const unsigned long long t2 = 3ull * (unsigned long long)S0i[ac][c] + 2ull * (unsigned long long)DSi[ac][c];
+      akW[c] = w62((2 * sc[c] + dsc[c]) >> 1);
+      const unsigned long long t2 = 3ull * (unsigned long long)sc[c] + 2ull * (unsigned long long)dsc[c];
       bkW[c] = w62(fix_mul_c((long long)(t2 >> 1), third62));
     }
-    const int st[3] = {jt.JY * jt.JZ, jt.JZ, 1};
-    const int base0 = comp * jt.nJ + lw[0] * st[0] + lw[1] * st[1] + lw[2] * st[2];
-    const int sm_ = st[comp], sb_ = st[ab], sc_ = st[ac];
-    const int nm = nw[comp] - 1, nb = nw[ab], nc = nw[ac];
+    const int base0 = comp * jt.nJ + base;
+    const int sm_ = c0 ? st[0] : (c1 ? st[1] : 1), sb_ = c0 ? st[1] : st[0], sc_ = comp == 2 ? st[1] : 1;
+    const int nm = (c0 ? nw[0] : (c1 ? nw[1] : nw[2])) - 1, nb = c0 ? nw[1] : nw[0], nc = comp == 2 ? nw[1] : nw[2];
 #pragma unroll
     for (int b = 0; b < 5; ++b) {
       if (b < nb) {
-        const long long sb = S0i[ab][b], db = DSi[ab][b];
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           if (c < nc) {
             FixAcc acc = fix_init();
-            fix_mac_c(acc, sb, akW[c]);
-            fix_mac_c(acc, db, bkW[c]);
+            fix_mac_c(acc, sb[b], akW[c]);
+            fix_mac_c(acc, db[b], bkW[c]);
             const W62 Aw = w62(max(fix_result(acc), 0LL));  // A >= 0; clamps a rounding below zero
 #pragma unroll
             for (int m = 0; m < 4; ++m)
@@ -299,12 +312,29 @@ __device__ __forceinline__ int push_particle(const Geom<T>& g, const Tiles& tl, 
         Wn[d][k] = w62(to_fixed(wn[d][k], 62));
         Wh[d][k] = w62(to_fixed(wh[d][k], 62));
       }
-    E[0] = from_fixed(gather_fixed<4, 4, 4>(sI + 0 * nS, SY, SZ, bh[0], bn[1], bn[2], Wh[0], Wn[1], Wn[2]), jt.fs[0]);
-    E[1] = from_fixed(gather_fixed<4, 4, 4>(sI + 1 * nS, SY, SZ, bn[0], bh[1], bn[2], Wn[0], Wh[1], Wn[2]), jt.fs[1]);
-    E[2] = from_fixed(gather_fixed<4, 4, 4>(sI + 2 * nS, SY, SZ, bn[0], bn[1], bh[2], Wn[0], Wn[1], Wh[2]), jt.fs[2]);
-    B[0] = from_fixed(gather_fixed<4, 4, 4>(sI + 3 * nS, SY, SZ, bn[0], bh[1], bh[2], Wn[0], Wh[1], Wh[2]), jt.fs[3]);
-    B[1] = from_fixed(gather_fixed<4, 4, 4>(sI + 4 * nS, SY, SZ, bh[0], bn[1], bh[2], Wh[0], Wn[1], Wh[2]), jt.fs[4]);
-    B[2] = from_fixed(gather_fixed<4, 4, 4>(sI + 5 * nS, SY, SZ, bh[0], bh[1], bn[2], Wh[0], Wh[1], Wn[2]), jt.fs[5]);
+    // one copy of the 4x4x4 gather in a loop over the six components (the
+    // unrolled six copies overflow the instruction cache); bit d of the
+    // component's mask = half-staggered along axis d (Ex x, Ey y, Ez z,
+    // Bx yz, By xz, Bz xy)
+#pragma unroll 1
+    for (int comp = 0; comp < 6; ++comp) {
+      const int hm = (0x356421 >> (4 * comp)) & 7;
+      W62 wx[4], wy[4], wz[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        wx[k] = (hm & 1) ? Wh[0][k] : Wn[0][k];
+        wy[k] = (hm & 2) ? Wh[1][k] : Wn[1][k];
+        wz[k] = (hm & 4) ? Wh[2][k] : Wn[2][k];
+      }
+      const double v = from_fixed(gather_fixed<4, 4, 4>(sI + comp * nS, SY, SZ, (hm & 1) ? bh[0] : bn[0],
+                                                        (hm & 2) ? bh[1] : bn[1], (hm & 4) ? bh[2] : bn[2], wx, wy, wz),
+                                  jt.fs[comp]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (comp == k) E[k] = v;
+        if (comp == k + 3) B[k] = v;
+      }
+    }
   } else {
     E[0] = gather_smem<4, 4, 4>(sF + 0 * nS, SY, SZ, bh[0], bn[1], bn[2], wh[0], wn[1], wn[2]);
     E[1] = gather_smem<4, 4, 4>(sF + 1 * nS, SY, SZ, bn[0], bh[1], bn[2], wn[0], wh[1], wn[2]);
@@ -477,11 +507,13 @@ __device__ __forceinline__ int push_particle(const Geom<T>& g, const Tiles& tl, 
 }
 
 // Threads per CTA of the push: FP32 256 (the cell-round order is built for
-// 256 threads; two CTAs of about 100 KB of shared memory per SM); FP64 256
-// (one CTA per SM: the FP64 tile takes most of the shared memory).
+// 256 threads; two CTAs of about 100 KB of shared memory per SM); FP64 512
+// (one CTA per SM, the FP64 tile takes most of the shared memory; 16 warps
+// at 128 registers hide the integer and fetch latencies better than 8 at
+// 254, despite a few hundred bytes of spills).
 template <typename T>
 constexpr int push_threads() {
-  return 256;
+  return sizeof(T) == 8 ? 512 : 256;
 }
 
 // One CTA per tile.  keys[p] receives the particle's tile after the move (or
