@@ -108,7 +108,10 @@ typedef struct pic_grid {
   double x0;            /* metres; lab-frame x of node 0 at t = 0              */
   int precision;        /* PIC_FP64 or PIC_FP32 (FP32: fields, momenta, offsets,
                            currents; the window accumulator and diagnostic
-                           reductions stay FP64)                              */
+                           reductions stay FP64).  FP64 gathers and deposits
+                           in 64-bit fixed point scaled per cell tile: the
+                           absolute precision of FP64 at the tile's largest
+                           field and current values                           */
   int bc_x;             /* PIC_BC_PERIODIC or PIC_BC_OPEN                      */
   int solver;           /* PIC_SOLVER_PERFECT (the paper's method) or
                            PIC_SOLVER_YEE (normal dispersion, for comparison;

@@ -150,9 +150,9 @@ __device__ __forceinline__ T gather_smem(const T* __restrict__ s, int SY, int SZ
 }
 
 // Comparisons of an offset against 0, 1/2 and 1.  In FP64 they are made on
-// the bit pattern with integer instructions, off the FP64 pipe that bounds
-// the push: for doubles of either sign the int64 view orders non-negative
-// values like the values and makes every negative value (and -0) negative.
+// the bit pattern with integer instructions, off the slow FP64 pipe: for
+// doubles of either sign the int64 view orders non-negative values like the
+// values and makes every negative value (and -0) negative.
 __device__ __forceinline__ bool lt_zero(double o) { return __double_as_longlong(o) < 0; }
 __device__ __forceinline__ bool ge_one(double o) { return __double_as_longlong(o) >= 0x3FF0000000000000LL; }
 __device__ __forceinline__ bool lt_half(double o) { return __double_as_longlong(o) < 0x3FE0000000000000LL; }
