@@ -43,9 +43,11 @@ FLOP_PER_PARTICLE = 1613
 ALG_BYTES_PER_PARTICLE = {"fp64": lambda ppc: 112 + 72 / ppc, "fp32": lambda ppc: 60 + 36 / ppc}
 # DRAM bytes (read + write) per particle of k_push_tiled, from one ncu capture
 # of the current kernel on a 256x128x128 window in a run's own state (run for
-# 256 steps past a load at rest), 8x8x8 tiles; traffic per launch scales with
-# the particles processed.
-NCU_TRAFFIC_PER_PARTICLE = {"fp64": (860.888576e6 + 1019.139e6) / 8336282, "fp32": (419.570688e6 + 273.255168e6) / 8336282}
+# 256 steps past a load at rest), 8x8x16 tiles; traffic per launch scales
+# with the particles processed.  None where the kernel has changed since its
+# capture (FP32: the float-to-fixed conversion of the deposit and the order
+# of the tile set-up; its last capture read 83.2 B per particle).
+NCU_TRAFFIC_PER_PARTICLE = {"fp64": (860.888576e6 + 1019.139e6) / 8336282, "fp32": None}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per particle (c1 spacings, 256x128x128 "
                   "window in a run's state) x particles per launch")
 LIMITER = {"fp64": ("issue latency and instruction fetch (ncu: issue active 36 %, FP64 pipe 30 %, integer ALU "
